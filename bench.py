@@ -1,0 +1,398 @@
+"""Benchmark of the grating-cloak renderer on one GB300 (or N, one rank per GPU).
+
+One step is one pass of the whole hot path on the 512 x 512, 4 samples per
+pixel workload (Lambda = 1, A = 0.04, cloak box 2 x 8 x 8, camera at 30 deg,
+RK4 h = Lambda/200, checkerboard background): the flat-mirror, bare-grating
+and cloaked-grating renders, their vertical centre lines (the FOV = 0 "2-D"
+case of Table 1), and C(0,0) of cloak vs mirror and bare vs mirror at FOV
+0/10/25/50 deg (Eqs. 14-15).  `value` is camera rays per second (Mrays/s) of
+the FP32 path over all ranks; the FP64 path, ray-steps/s, the latency of each
+step, the roofline of the dominant kernel and the CPU oracle on the host are
+reported beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1012_5107_gb300 import inputs  # noqa: E402
+
+FOVS = [0.0, 10.0, 25.0, 50.0]
+SIDE, SPP = 512, 4
+WORKLOAD = "grating cloak 512x512 4spp RK4 h=L/200, mirror+bare+cloak + centre lines + C(0,0) at 0/10/25/50 deg"
+
+# Algorithmic FP32 operations (FMA = 2) per unit of work of the render kernel;
+# the counters of one launch give the units (see the kernel's w0_solve,
+# ray_force, w0_predict and rk4_step).
+FLOP_PER_NEWTON = 30
+FLOP_PER_EVAL = 47
+FLOP_PER_STEP = 81
+MUFU_PER_NEWTON = 4
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        return json.load(open(p)), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def scenes_for(precision: int) -> dict:
+    base = inputs.config_main(precision=precision)
+    out = {}
+    for kind, p in inputs.three_renders(base).items():
+        out[kind] = p
+        out[kind + "_line"] = dict(p, centre_line=1)
+    return out
+
+
+class Step:
+    """Device buffers and scenes of one pass of the hot path."""
+
+    def __init__(self, rt, torch, precision: int, stream):
+        self.rt, self.torch, self.stream = rt, torch, stream
+        self.params = scenes_for(precision)
+        self.scenes = {k: rt.Scene(p) for k, p in self.params.items()}
+        self.img = {k: torch.zeros(s.shape, dtype=torch.float32, device="cuda") for k, s in self.scenes.items()}
+        self.c_full = torch.zeros((2, 3, 4), dtype=torch.float64, device="cuda")
+        self.c_line = torch.zeros((2, 1, 4), dtype=torch.float64, device="cuda")
+        self.rays = sum(s.height * s.wout * s.spp for s in self.scenes.values())
+        # launches of our kernels per step: 6 renders + 4 cross-correlation calls of 2 kernels each
+        self.launches = len(self.scenes) + 4 * 2
+
+    def run(self, ev_cloak=None):
+        rt, st = self.rt, self.stream
+        for k, s in self.scenes.items():
+            if k == "cloak" and ev_cloak is not None:
+                ev_cloak[0].record(st)
+                s.render(self.img[k], stream=st)
+                ev_cloak[1].record(st)
+            else:
+                s.render(self.img[k], stream=st)
+        for q, g in enumerate(("cloak", "bare")):
+            rt.xcorr(self.img["mirror"], self.img[g], FOVS[1:], 50.0, out=self.c_full[q], stream=st)
+            rt.xcorr(self.img["mirror_line"], self.img[g + "_line"], FOVS[:1], 50.0, out=self.c_line[q], stream=st)
+
+    def stats(self) -> dict:
+        tot = {}
+        for k, s in self.scenes.items():
+            for key, v in s.stats().items():
+                if key == "status":
+                    continue
+                tot[key] = tot.get(key, 0) + v
+        return tot
+
+    def cvalues(self) -> dict:
+        full = self.c_full.cpu().numpy()
+        line = self.c_line.cpu().numpy()
+        out = {}
+        for q, g in enumerate(("cloak", "bare")):
+            out[f"C_{g}_vs_mirror"] = {"0": float(line[q, 0, 3]), "10": float(full[q, 0, 3]),
+                                       "25": float(full[q, 1, 3]), "50": float(full[q, 2, 3])}
+        return out
+
+
+def flush_l2(torch, buf):
+    buf.add_(1)
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    from paper_1012_5107_gb300 import build as B
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1012_5107_gb300 import rt
+    rt.lib()
+    dev = torch.cuda.current_device()
+    stream = torch.cuda.Stream()
+    flush = torch.zeros(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")   # 256 MiB > L2
+
+    step = Step(rt, torch, inputs.FP32, stream)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step.run()
+            flush_l2(torch, flush)
+    torch.cuda.synchronize()
+    stats = step.stats()
+
+    clocks = Clocks(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    evc = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    t_wall = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i in range(args.steps):
+            evs[i][0].record(stream)
+            step.run(ev_cloak=evc[i])
+            evs[i][1].record(stream)
+            flush_l2(torch, flush)
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = np.array([a.elapsed_time(b) for a, b in evs])
+    cloak_ms = np.array([a.elapsed_time(b) for a, b in evc])
+    total_ms = float(step_ms.sum())
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    ms_per_step = total_ms / args.steps
+    rays_per_step = step.rays * world
+    value = rays_per_step / (ms_per_step * 1e-3) / 1e6
+    steps_per_s = stats["steps"] * world / (ms_per_step * 1e-3)
+    cvals = step.cvalues()
+
+    # roofline of the dominant kernel (cloaked-grating render)
+    cst = step.scenes["cloak"].stats()
+    flop = FLOP_PER_NEWTON * cst["newton"] + FLOP_PER_EVAL * cst["evals"] + FLOP_PER_STEP * cst["steps"]
+    cl_ms = float(np.mean(cloak_ms))
+    pk, pk_kind = peaks()
+    clock_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak_tflops = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
+    achieved = flop / (cl_ms * 1e-3) / 1e12
+    mufu = MUFU_PER_NEWTON * cst["newton"]
+    mufu_peak = 152 * 16 * clock_mhz * 1e6
+    roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                "kernel": "render_kernel<float> (cloaked grating)",
+                "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max clock of {pk_kind} peaks file)",
+                "mufu_frac": round(mufu / (cl_ms * 1e-3) / mufu_peak, 4),
+                "kernel_ms": round(cl_ms, 3)}
+
+    # FP64 path on the cloaked render (the dominant kernel), one warm-up and a few timed launches
+    fp64 = None
+    if not args.no_fp64:
+        p64 = inputs.three_renders(inputs.config_main(precision=inputs.FP64))["cloak"]
+        s64 = rt.Scene(p64)
+        img = torch.zeros(s64.shape, dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            s64.render(img, stream=stream)
+        torch.cuda.synchronize()
+        n64 = 2
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(n64):
+                s64.render(img, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        st64 = s64.stats()
+        fp64 = {"cloak_ms": round(ms64, 3), "Mrays_per_s": round(st64["rays"] / (ms64 * 1e-3) / 1e6, 3),
+                "Gsteps_per_s": round(st64["steps"] / (ms64 * 1e-3) / 1e9, 4)}
+    fp32_cloak = {"cloak_ms": round(cl_ms, 3), "Mrays_per_s": round(cst["rays"] / (cl_ms * 1e-3) / 1e6, 3),
+                  "Gsteps_per_s": round(cst["steps"] / (cl_ms * 1e-3) / 1e9, 4)}
+
+    # end to end through the C ABI: renders, device-to-host copies of the images and of C
+    host = {k: torch.empty(s.shape, dtype=torch.float32, pin_memory=True) for k, s in step.scenes.items()}
+    hc = torch.empty((2, 3, 4), dtype=torch.float64, pin_memory=True)
+    hl = torch.empty((2, 1, 4), dtype=torch.float64, pin_memory=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    n_e2e = max(1, min(args.steps, 5))
+    for _ in range(n_e2e):
+        with torch.cuda.stream(stream):
+            step.run()
+            for k in host:
+                host[k].copy_(step.img[k], non_blocking=True)
+            hc.copy_(step.c_full, non_blocking=True)
+            hl.copy_(step.c_line, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - t0) / n_e2e
+    d2h = sum(h.numel() * 4 for h in host.values()) + hc.numel() * 8 + hl.numel() * 8
+    h2d = len(step.scenes) * 512      # scene parameters travel with each launch (DevScene by value)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_seconds)
+
+    lat = {"p50_ms": round(float(np.percentile(step_ms, 50)), 3), "p99_ms": round(float(np.percentile(step_ms, 99)), 3)}
+    line = {
+        "metric": "Mrays/s (FP32 path; ray-steps/s and FP64 path alongside) at <=1e-4 Lambda error; p50/p99 frame latency",
+        "value": round(value, 3), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(ms_per_step, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "width": SIDE, "height": SIDE, "spp": SPP, "rays_per_step": rays_per_step,
+                   "integrator": "RK4 h=Lambda/200", "l2": "flushed between steps (256 MiB write)",
+                   "parallelism": f"replicas x{world}"},
+        "ray_steps_per_s": round(steps_per_s, 1),
+        "frame_latency": lat,
+        "fp32_cloak_render": fp32_cloak, "fp64_cloak_render": fp64,
+        "fp32_over_fp64_steps": (round(fp32_cloak["Gsteps_per_s"] / fp64["Gsteps_per_s"], 2) if fp64 else None),
+        "C": cvals,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": {"value": round(rays_per_step / e2e_s / 1e6, 3), "unit": "Mrays/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": step.launches * args.steps,
+        "clocks": clk,
+        "wall_s_timed": round(t_wall, 3),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def cpu_baseline(seconds: float) -> dict:
+    """The FP64 oracle as it stands, on the host cores, over a seeded pixel sample
+    of the cloaked-grating render (the dominant part of a step)."""
+    from oracle import oracle as orc
+    orc.build()
+    p = inputs.three_renders(inputs.config_main(precision=inputs.FP64))["cloak"]
+    sc = orc.Scene(p)
+    cores = orc.max_threads()
+    n = 256
+    t = 0.0
+    total_rays, total_t = 0, 0.0
+    while True:
+        pix = inputs.pixel_subset(SIDE, SIDE, n, seed=99)
+        t0 = time.perf_counter()
+        orc.render_pixels(sc, pix, nthreads=cores)
+        t = time.perf_counter() - t0
+        total_rays += n * SPP
+        total_t += t
+        if total_t >= seconds or n >= SIDE * SIDE:
+            break
+        n = min(SIDE * SIDE, int(n * max(2.0, min(8.0, seconds / max(t, 1e-3) / 2))))
+    return {"value": round(total_rays / total_t / 1e6, 5), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+            "sample": f"cloaked-grating render of the 512x512 4spp workload, seeded pixel subsets "
+                      f"(last {n} pixels), {total_rays} rays in {total_t:.1f} s"}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if world > 1 and rank != 0:
+        return
+    from oracle import oracle as orc
+    orc.build()
+    p = inputs.three_renders(inputs.config_main(precision=inputs.FP64))
+    cores = orc.max_threads()
+    npix = 96   # per render per step: a bounded sample of the workload
+    scenes = {k: orc.Scene(v) for k, v in p.items()}
+    for _ in range(args.warmup):
+        for k, sc in scenes.items():
+            orc.render_pixels(sc, inputs.pixel_subset(SIDE, SIDE, npix, seed=7), nthreads=cores)
+    times = []
+    for i in range(args.steps):
+        t0 = time.perf_counter()
+        for k, sc in scenes.items():
+            orc.render_pixels(sc, inputs.pixel_subset(SIDE, SIDE, npix, seed=100 + i), nthreads=cores)
+        times.append(time.perf_counter() - t0)
+    rays = 3 * npix * SPP
+    ms = float(np.mean(times)) * 1e3
+    v = rays / (ms * 1e-3) / 1e6
+    line = {"impl": "reference",
+            "metric": "Mrays/s (FP32 path; ray-steps/s and FP64 path alongside) at <=1e-4 Lambda error; p50/p99 frame latency",
+            "value": round(v, 5), "unit": "Mrays/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "width": SIDE, "height": SIDE, "spp": SPP,
+                       "sample": f"{npix} seeded pixels per render per step"},
+            "cpu_baseline": {"value": round(v, 5), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+                             "sample": f"{npix} seeded pixels x {SPP} spp of each of the three renders per step"},
+            "e2e": {"value": round(v, 5), "unit": "Mrays/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gratingrt", choices=["gratingrt", "reference"])
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

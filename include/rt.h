@@ -1,0 +1,212 @@
+/*
+ * rt.h -- C ABI of the GB300 (sm_103a) renderer for Newtonian ray tracing of
+ * the conformal grating cloak (Halimeh, Schmied & Wegener, Opt. Express 2010).
+ *
+ * Method (paper section / equation):
+ *   - refractive index n = 1/|1 + W0(i c k exp(i k (x + i y)))|, c = i A,
+ *     k = 2 pi / Lambda (Sec. 2, Eq. 1; W0 is the principal Lambert branch,
+ *     Eq. 13) and its gradient (Sec. 3, Eq. 12);
+ *   - each ray is a particle obeying Newton's law derived from Fermat's
+ *     principle (Sec. 3, Eqs. 9-11), integrated numerically inside the cloak
+ *     and straight in air, refracted by Snell's law at the cloak boundary
+ *     (Sec. 3);
+ *   - the metal grating is the trochoid of Eq. 2 (Sec. 2), a mirror;
+ *   - frames are compared by the image cross-correlation C of Eqs. 14-15
+ *     (Sec. 5), C(0,0) over central horizontal fields of view (Table 1).
+ *
+ * Conventions.  All lengths are world units; Lambda sets the scale (renders
+ * are invariant under a common scaling of every length).  x runs across the
+ * grooves, y is the mirror normal, z runs along the grooves.  The cloak is
+ * the box |x| <= E/2, |z| <= E/2, -A <= y <= -A + H; n = 1 outside it.
+ *
+ * Ownership.  Every pointer argument named d_* is device memory owned by the
+ * caller; h_* is host memory owned by the caller.  The library owns what it
+ * allocates inside an rt_scene (texture copy, work counters, statistics) and
+ * frees it in rt_destroy_scene.  Scenes may be used from one host thread at
+ * a time.
+ *
+ * Streams.  `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Device-side work is enqueued asynchronously on it unless the
+ * function says otherwise.
+ *
+ * Errors.  Functions return RT_OK (0) or a negative code; rt_last_error()
+ * gives a message for the calling thread.  Nothing exits or aborts.  There is
+ * no CPU fallback: without an sm_103 device the compute functions return
+ * RT_ENODEV.
+ */
+#ifndef GRATINGRT_RT_H
+#define GRATINGRT_RT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* return codes */
+#define RT_OK 0
+#define RT_PENDING 1          /* rt_poll: the request is not finished yet      */
+#define RT_EINVAL (-22)       /* invalid argument or descriptor                */
+#define RT_ENOMEM (-12)       /* device or host allocation failed              */
+#define RT_ENODEV (-19)       /* no sm_103 device current                      */
+#define RT_EBUSY (-16)        /* rt_submit: over the ray-state budget          */
+#define RT_ETIMEDOUT (-110)   /* a bounded wait ran out                        */
+#define RT_ECUDA (-5)         /* a CUDA runtime call failed (see message)      */
+
+/* scene kinds and options */
+#define RT_MIRROR_FLAT 0      /* plane y = 0 (Fig. 3a)                         */
+#define RT_MIRROR_TROCHOID 1  /* trochoid grating, Eq. 2 (Fig. 3b, 3c)         */
+#define RT_BG_CHECKER 0       /* two-colour checkerboard                       */
+#define RT_BG_TEXTURE 1       /* greyscale texture, bilinear, wrapping         */
+#define RT_RK4 0              /* classical Runge-Kutta, fixed step h           */
+#define RT_DP45 1             /* Dormand-Prince 5(4), adaptive (rtol, atol)    */
+#define RT_FP32 0             /* single precision bulk arithmetic              */
+#define RT_FP64 1             /* double precision throughout                   */
+
+/* per-ray status */
+#define RT_RAY_OK 0           /* reached the background                        */
+#define RT_RAY_SKY 1          /* left the scene away from the background       */
+#define RT_RAY_MAX_BOUNCES 2  /* more than max_bounces reflections             */
+#define RT_RAY_MAX_STEPS 3    /* more than max_steps integrator steps          */
+#define RT_RAY_NAN 4          /* non-finite state                              */
+
+/*
+ * Scene descriptor.  The camera is a pinhole at distance cam_dist from the
+ * origin at elevation elev_deg and azimuth azim_deg, looking at the origin,
+ * with horizontal full field of view hfov_deg and square pixels (Sec. 4).
+ * The background stands in for the photograph of Fig. 2(a): a plane normal to
+ * the mirrored view axis, cam_dist from the origin.  Ray directions of sample
+ * s of pixel (i, j): pixel centre for spp = 1, one uniform offset in each cell
+ * of an m x m grid for spp = m^2 and two uniforms otherwise, drawn from
+ * SplitMix64 outputs 2c+1 and 2c+2 with c = ((scene_id*height + i)*width_out
+ * + j)*spp + s (width_out = 1 for centre_line).
+ */
+typedef struct rt_scene_desc {
+    double Lambda;            /* grating period (> 0)                           */
+    double A;                 /* half peak-to-peak amplitude, 0 <= kA < 1       */
+    double H, E;              /* cloak box height above y=-A and x/z extent     */
+    double cam_dist, elev_deg, azim_deg, hfov_deg;
+    double bg_cell;           /* checkerboard cell size                         */
+    double tex_texel;         /* texture texel size                             */
+    double colour0[3], colour1[3];  /* checkerboard colours, linear [0, 1]      */
+    double h;                 /* RK4 step (in the ray parameter tau, |dr/dtau| = n); DP45 first step */
+    double rtol, atol;        /* DP45 tolerances (atol in world length units)   */
+    double h_max;             /* DP45 largest step                              */
+    uint64_t seed, scene_id;  /* jitter stream                                  */
+    int64_t max_steps;        /* guard on integrator steps per ray              */
+    const float* tex;         /* host, tex_size^2 row-major greyscale (TEXTURE) */
+    int32_t mirror;           /* RT_MIRROR_*                                    */
+    int32_t cloak;            /* 1: graded-index cloak box present              */
+    int32_t width, height;    /* image size                                     */
+    int32_t spp;              /* samples per pixel                              */
+    int32_t centre_line;      /* 1: render only the vertical centre line
+                                 (height x 1 image, horizontal offset 0)        */
+    int32_t background;       /* RT_BG_*                                        */
+    int32_t tex_size;         /* texture side                                   */
+    int32_t integrator;       /* RT_RK4 | RT_DP45                               */
+    int32_t precision;        /* RT_FP32 | RT_FP64                              */
+    int32_t max_bounces;      /* guard on reflections per ray                   */
+    int32_t flags;            /* reserved, 0                                    */
+} rt_scene_desc;
+
+/* Per-sample exit record: where the ray's final straight segment crosses the
+   plane y = -A + H + Lambda (or its last point if it does not), its unit
+   direction, colour and counters. */
+typedef struct rt_ray_record {
+    double pos[3];
+    double dir[3];
+    float rgb[3];
+    int32_t status;           /* RT_RAY_*                                       */
+    int32_t bounces;          /* reflections (grating, mirror, total)           */
+    int32_t events;           /* located events inside the cloak                */
+    int64_t steps;            /* integrator steps (accepted + rejected)         */
+} rt_ray_record;
+
+/* Counters accumulated over one rt_render call. */
+typedef struct rt_stats {
+    uint64_t rays;            /* camera samples traced                          */
+    uint64_t steps;           /* integrator steps                               */
+    uint64_t evals;           /* index/gradient evaluations                     */
+    uint64_t newton;          /* W0 iterations                                  */
+    uint64_t events;          /* located events                                 */
+    uint64_t fp64_refine;     /* W0 refinements in FP64 near the branch point   */
+    uint64_t status[5];       /* rays per RT_RAY_* status                       */
+} rt_stats;
+
+typedef struct rt_scene rt_scene;
+
+/*
+ * rt_create_scene: validate `desc` and build a scene on the current device:
+ * copies the texture (if any) to device memory and allocates the scene's work
+ * counters.  Synchronous.  Returns RT_EINVAL for an invalid descriptor
+ * (message names the field), RT_ENODEV without an sm_103 device, RT_ENOMEM.
+ */
+int rt_create_scene(const rt_scene_desc* desc, rt_scene** out);
+
+/* rt_destroy_scene: free the scene (waits for its outstanding work). NULL is a no-op. */
+void rt_destroy_scene(rt_scene* scene);
+
+/*
+ * rt_render: render the whole image (Sec. 4; Figs. 3-7).
+ *   d_rgb   height x width_out x 3 float, mean colour per pixel (linear)
+ *   d_rgb8  nullable, height x width_out x 3 bytes, q = floor(clamp(c)*255+1/2)
+ *   d_rec   nullable, height x width_out x spp records in sample order
+ * Asynchronous on `stream`.  Counters of the call can be read with
+ * rt_scene_stats once the stream has completed.
+ */
+int rt_render(rt_scene* scene, float* d_rgb, uint8_t* d_rgb8, rt_ray_record* d_rec, void* stream);
+
+/*
+ * rt_render_pixels: render the listed pixels only (flat indices i*width_out+j,
+ * device array d_pix of npix entries); d_rgb is npix x 3, d_rec (nullable)
+ * npix x spp.  Same arithmetic as rt_render for those pixels.
+ */
+int rt_render_pixels(rt_scene* scene, const int64_t* d_pix, int64_t npix, float* d_rgb,
+                     rt_ray_record* d_rec, void* stream);
+
+/*
+ * rt_render_host: rt_render into library-owned device buffers followed by the
+ * copy of the colours (height x width_out x 3 float) and, if h_rgb8 is not
+ * NULL, the 8-bit image to host memory; waits for `stream`.
+ */
+int rt_render_host(rt_scene* scene, float* h_rgb, uint8_t* h_rgb8, void* stream);
+
+/* rt_scene_stats: counters of the last render of this scene (waits for it). */
+int rt_scene_stats(rt_scene* scene, rt_stats* out);
+
+/*
+ * rt_xcorr: image cross-correlation C(0,0) of Eqs. 14-15 (Sec. 5) between
+ * the reference d_f and d_g (both height x width x channels float, device).
+ * For each of the n_fov fields of view fov_deg[q] (host array, degrees) the
+ * window is the columns whose pixel-centre horizontal angle is within
+ * fov/2 of the image centre for a camera of horizontal field hfov_deg (a
+ * width-1 centre-line image has its one column at angle 0).  Per window and
+ * channel c: C_c = sum (f-<f>)(g-<g>) / sum (f-<f>)^2 with the means over the
+ * window (Eq. 14); the last entry treats the channels as one stacked image.
+ * Writes n_fov x (channels+1) doubles to d_out (device).  Empty windows give
+ * NaN.  Asynchronous; uses scratch owned by the library.
+ */
+int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, int32_t channels,
+             const double* fov_deg, int32_t n_fov, double hfov_deg, double* d_out, void* stream);
+
+/*
+ * rt_eval_medium: W0, n and the ray force grad(n^2)/2 at npoints points
+ * (device d_xy: x0,y0,x1,y1,..., world units) for grating period Lambda and
+ * amplitude A (Eqs. 1, 12, 13).  d_out gets per point
+ * (Re W0, Im W0, n, F_x, F_y) in world units.  precision RT_FP32 | RT_FP64.
+ */
+int rt_eval_medium(int32_t precision, double Lambda, double A, const double* d_xy, int64_t npoints,
+                   double* d_out, void* stream);
+
+/* rt_last_error: message of the last failing call on this thread ("" if none). */
+const char* rt_last_error(void);
+
+/* rt_version: library version string. */
+const char* rt_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GRATINGRT_RT_H */

@@ -1,0 +1,331 @@
+// rt_api.cu -- host runtime behind the C ABI of include/rt.h: descriptor
+// validation, scene tables on the device, launches, counters and errors.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+
+#include "rt_internal.h"
+
+namespace grt {
+
+static thread_local char g_err[512];
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+#define RT_CK(call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));            \
+            return RT_ECUDA;                                                                          \
+        }                                                                                             \
+    } while (0)
+
+#define RT_REQ(cond, ...)                                                                             \
+    do {                                                                                              \
+        if (!(cond)) {                                                                                \
+            set_error(__VA_ARGS__);                                                                   \
+            return RT_EINVAL;                                                                         \
+        }                                                                                             \
+    } while (0)
+
+struct rt_scene {
+    rt_scene_desc desc;
+    DevScene dev;
+    int device;
+    int grid;
+    float* d_tex;
+    unsigned long long* d_counters;
+    float* d_host_rgb;        // buffers of rt_render_host
+    uint8_t* d_host_rgb8;
+    cudaEvent_t done;
+    bool rendered;
+};
+
+static int current_device(int* dev)
+{
+    cudaError_t e = cudaGetDevice(dev);
+    if (e != cudaSuccess) {
+        set_error("no CUDA device: %s", cudaGetErrorString(e));
+        return RT_ENODEV;
+    }
+    int major = 0, minor = 0;
+    cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, *dev);
+    cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, *dev);
+    if (major != 10 || minor != 3) {
+        set_error("device %d is sm_%d%d; this library is built for sm_103a only", *dev, major, minor);
+        return RT_ENODEV;
+    }
+    return RT_OK;
+}
+
+static int validate(const rt_scene_desc* d)
+{
+    RT_REQ(d, "desc is NULL");
+    RT_REQ(d->Lambda > 0.0 && std::isfinite(d->Lambda), "Lambda must be finite and > 0");
+    const double kA = 2.0 * kPi * d->A / d->Lambda;
+    RT_REQ(d->A >= 0.0 && kA < 1.0, "A must satisfy 0 <= 2 pi A / Lambda < 1 (curtate trochoid)");
+    RT_REQ(d->mirror == RT_MIRROR_FLAT || d->mirror == RT_MIRROR_TROCHOID, "mirror must be RT_MIRROR_FLAT or RT_MIRROR_TROCHOID");
+    RT_REQ(d->cloak == 0 || d->cloak == 1, "cloak must be 0 or 1");
+    RT_REQ(!d->cloak || d->mirror == RT_MIRROR_TROCHOID, "the cloak needs the trochoid mirror");
+    RT_REQ(!d->cloak || (d->H > 2.0 * d->A && d->E > 0.0 && std::isfinite(d->H) && std::isfinite(d->E)),
+           "cloak box needs H > 2A and E > 0");
+    RT_REQ(d->width >= 1 && d->height >= 1 && d->spp >= 1, "width, height and spp must be >= 1");
+    RT_REQ(d->centre_line == 0 || d->centre_line == 1, "centre_line must be 0 or 1");
+    RT_REQ(d->hfov_deg > 0.0 && d->hfov_deg < 180.0, "hfov_deg must be in (0, 180)");
+    RT_REQ(d->cam_dist > 0.0 && std::isfinite(d->cam_dist), "cam_dist must be > 0");
+    RT_REQ(d->elev_deg >= -90.0 && d->elev_deg <= 90.0 && std::fabs(std::cos(d->elev_deg * kPi / 180.0)) > 1e-9,
+           "elev_deg must be in (-90, 90)");
+    RT_REQ(std::isfinite(d->azim_deg), "azim_deg must be finite");
+    RT_REQ(d->integrator == RT_RK4 || d->integrator == RT_DP45, "integrator must be RT_RK4 or RT_DP45");
+    RT_REQ(d->integrator == RT_RK4, "RT_DP45 is not available in this build");
+    RT_REQ(d->precision == RT_FP32 || d->precision == RT_FP64, "precision must be RT_FP32 or RT_FP64");
+    RT_REQ(d->h > 0.0 && std::isfinite(d->h), "h must be > 0");
+    if (d->integrator == RT_DP45)
+        RT_REQ(d->rtol > 0.0 && d->atol > 0.0 && d->h_max > 0.0, "DP45 needs rtol, atol, h_max > 0");
+    RT_REQ(d->background == RT_BG_CHECKER || d->background == RT_BG_TEXTURE, "background must be RT_BG_*");
+    if (d->background == RT_BG_CHECKER) RT_REQ(d->bg_cell > 0.0, "bg_cell must be > 0");
+    else RT_REQ(d->tex && d->tex_size > 0 && d->tex_texel > 0.0, "texture background needs tex, tex_size, tex_texel");
+    RT_REQ(d->max_bounces >= 0 && d->max_steps >= 1, "max_bounces >= 0 and max_steps >= 1");
+    RT_REQ(d->flags == 0, "flags must be 0");
+    const double wout = d->centre_line ? 1.0 : (double)d->width;
+    RT_REQ((double)d->height * wout * (double)d->spp < 4.0e18, "image too large");
+    return RT_OK;
+}
+
+static void build_dev(const rt_scene_desc* d, DevScene* s)
+{
+    memset(s, 0, sizeof *s);
+    const double L = d->Lambda;
+    s->Lambda = L;
+    s->A = d->A / L;
+    s->kA = kTwoPi * s->A;
+    s->H = d->H / L;
+    s->E2 = 0.5 * d->E / L;
+    s->ytop = -s->A + s->H;
+    s->yrec = -s->A + s->H + 1.0;
+    const double te = d->elev_deg * kPi / 180.0, ph = d->azim_deg * kPi / 180.0, D = d->cam_dist / L;
+    s->C[0] = -D * cos(te) * cos(ph);
+    s->C[1] = D * sin(te);
+    s->C[2] = -D * cos(te) * sin(ph);
+    for (int a = 0; a < 3; ++a) s->f[a] = -s->C[a] / D;
+    // r = f x y_hat normalised, u = r x f
+    double r[3] = {-s->f[2], 0.0, s->f[0]};
+    const double rl = sqrt(r[0] * r[0] + r[2] * r[2]);
+    for (int a = 0; a < 3; ++a) s->r[a] = r[a] / rl;
+    s->u[0] = s->r[1] * s->f[2] - s->r[2] * s->f[1];
+    s->u[1] = s->r[2] * s->f[0] - s->r[0] * s->f[2];
+    s->u[2] = s->r[0] * s->f[1] - s->r[1] * s->f[0];
+    s->tx = tan(0.5 * d->hfov_deg * kPi / 180.0);
+    s->ty = s->tx * (double)d->height / (double)d->width;
+    s->fr[0] = s->f[0]; s->fr[1] = -s->f[1]; s->fr[2] = s->f[2];
+    s->ur[0] = s->r[1] * s->fr[2] - s->r[2] * s->fr[1];
+    s->ur[1] = s->r[2] * s->fr[0] - s->r[0] * s->fr[2];
+    s->ur[2] = s->r[0] * s->fr[1] - s->r[1] * s->fr[0];
+    for (int a = 0; a < 3; ++a) s->Pb[a] = D * s->fr[a];
+    s->cell = d->bg_cell / L;
+    s->texel = d->tex_texel / L;
+    s->h = d->h / L;
+    s->rtol = d->rtol;
+    s->atol = d->atol / L;
+    s->hmax = d->h_max / L;
+    for (int a = 0; a < 3; ++a) { s->col0[a] = (float)d->colour0[a]; s->col1[a] = (float)d->colour1[a]; }
+    s->seed = d->seed;
+    s->scene_id = d->scene_id;
+    s->max_steps = d->max_steps;
+    s->mirror = d->mirror;
+    s->cloak = d->cloak;
+    s->width = d->width;
+    s->height = d->height;
+    s->wout = d->centre_line ? 1 : d->width;
+    s->spp = d->spp;
+    int m = (int)floor(sqrt((double)d->spp) + 0.5);
+    s->m = (m * m == d->spp) ? m : 0;
+    s->centre_line = d->centre_line;
+    s->background = d->background;
+    s->tex_size = d->tex_size;
+    s->integrator = d->integrator;
+    s->max_bounces = d->max_bounces;
+    s->nwork = (int64_t)d->height * s->wout;
+}
+
+extern "C" {
+
+const char* rt_last_error(void) { return g_err; }
+
+const char* rt_version(void) { return "gratingrt 0.1 (sm_103a)"; }
+
+int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
+{
+    g_err[0] = 0;
+    RT_REQ(out, "out is NULL");
+    *out = nullptr;
+    int rc = validate(desc);
+    if (rc) return rc;
+    int dev;
+    rc = current_device(&dev);
+    if (rc) return rc;
+    rt_scene* s = (rt_scene*)calloc(1, sizeof(rt_scene));
+    if (!s) { set_error("host allocation failed"); return RT_ENOMEM; }
+    s->desc = *desc;
+    s->desc.tex = nullptr;
+    s->device = dev;
+    build_dev(desc, &s->dev);
+    int bps = 0;
+    cudaError_t e = render_occupancy(desc->precision, &bps);
+    int nsm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess && desc->background == RT_BG_TEXTURE) {
+        const size_t bytes = (size_t)desc->tex_size * desc->tex_size * sizeof(float);
+        e = cudaMalloc(&s->d_tex, bytes);
+        if (e == cudaSuccess) e = cudaMemcpy(s->d_tex, desc->tex, bytes, cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) e = cudaMalloc(&s->d_counters, kCounters * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(s->d_counters, 0, kCounters * sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->done, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+        set_error("rt_create_scene: %s", cudaGetErrorString(e));
+        rt_destroy_scene(s);
+        return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+    }
+    s->dev.tex = s->d_tex;
+    s->grid = (bps > 0 ? bps : 1) * nsm;
+    *out = s;
+    return RT_OK;
+}
+
+void rt_destroy_scene(rt_scene* s)
+{
+    if (!s) return;
+    if (s->done) cudaEventSynchronize(s->done);
+    if (s->d_tex) cudaFree(s->d_tex);
+    if (s->d_counters) cudaFree(s->d_counters);
+    if (s->d_host_rgb) cudaFree(s->d_host_rgb);
+    if (s->d_host_rgb8) cudaFree(s->d_host_rgb8);
+    if (s->done) cudaEventDestroy(s->done);
+    free(s);
+}
+
+static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float* d_rgb, uint8_t* d_rgb8,
+                         rt_ray_record* d_rec, void* stream)
+{
+    RT_REQ(s, "scene is NULL");
+    RT_REQ(d_rgb || nwork == 0, "d_rgb is NULL");
+    int dev;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    RT_REQ(dev == s->device, "scene was created on device %d, current device is %d", s->device, dev);
+    cudaStream_t st = (cudaStream_t)stream;
+    DevScene sc = s->dev;
+    sc.pix_list = d_pix;
+    sc.nwork = nwork;
+    RT_CK(cudaMemsetAsync(s->d_counters, 0, kCounters * sizeof(unsigned long long), st));
+    if (nwork > 0) RT_CK(launch_render(sc, s->desc.precision, d_rgb, d_rgb8, d_rec, s->d_counters, s->grid, st));
+    RT_CK(cudaEventRecord(s->done, st));
+    s->rendered = true;
+    return RT_OK;
+}
+
+int rt_render(rt_scene* s, float* d_rgb, uint8_t* d_rgb8, rt_ray_record* d_rec, void* stream)
+{
+    g_err[0] = 0;
+    RT_REQ(s, "scene is NULL");
+    return render_common(s, nullptr, s->dev.nwork, d_rgb, d_rgb8, d_rec, stream);
+}
+
+int rt_render_pixels(rt_scene* s, const int64_t* d_pix, int64_t npix, float* d_rgb, rt_ray_record* d_rec,
+                     void* stream)
+{
+    g_err[0] = 0;
+    RT_REQ(npix >= 0, "npix must be >= 0");
+    RT_REQ(npix == 0 || d_pix, "d_pix is NULL");
+    return render_common(s, d_pix, npix, d_rgb, nullptr, d_rec, stream);
+}
+
+int rt_render_host(rt_scene* s, float* h_rgb, uint8_t* h_rgb8, void* stream)
+{
+    g_err[0] = 0;
+    RT_REQ(s && h_rgb, "scene and h_rgb must not be NULL");
+    const size_t n = (size_t)s->dev.nwork * 3;
+    if (!s->d_host_rgb) RT_CK(cudaMalloc(&s->d_host_rgb, n * sizeof(float)));
+    if (h_rgb8 && !s->d_host_rgb8) RT_CK(cudaMalloc(&s->d_host_rgb8, n));
+    cudaStream_t st = (cudaStream_t)stream;
+    int rc = render_common(s, nullptr, s->dev.nwork, s->d_host_rgb, h_rgb8 ? s->d_host_rgb8 : nullptr, nullptr,
+                           stream);
+    if (rc) return rc;
+    RT_CK(cudaMemcpyAsync(h_rgb, s->d_host_rgb, n * sizeof(float), cudaMemcpyDeviceToHost, st));
+    if (h_rgb8) RT_CK(cudaMemcpyAsync(h_rgb8, s->d_host_rgb8, n, cudaMemcpyDeviceToHost, st));
+    RT_CK(cudaStreamSynchronize(st));
+    return RT_OK;
+}
+
+int rt_scene_stats(rt_scene* s, rt_stats* out)
+{
+    g_err[0] = 0;
+    RT_REQ(s && out, "scene and out must not be NULL");
+    unsigned long long c[kCounters];
+    RT_CK(cudaEventSynchronize(s->done));
+    RT_CK(cudaMemcpy(c, s->d_counters, sizeof c, cudaMemcpyDeviceToHost));
+    out->rays = c[1];
+    out->steps = c[2];
+    out->evals = c[3];
+    out->newton = c[4];
+    out->events = c[5];
+    out->fp64_refine = c[6];
+    for (int q = 0; q < 5; ++q) out->status[q] = c[7 + q];
+    return RT_OK;
+}
+
+int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, int32_t channels,
+             const double* fov_deg, int32_t n_fov, double hfov_deg, double* d_out, void* stream)
+{
+    g_err[0] = 0;
+    RT_REQ(d_f && d_g && d_out && fov_deg, "null pointer argument");
+    RT_REQ(height >= 1 && width >= 1, "height and width must be >= 1");
+    RT_REQ(channels >= 1 && channels <= 4, "channels must be 1..4");
+    RT_REQ(n_fov >= 1 && n_fov <= kMaxWindows, "n_fov must be 1..%d", kMaxWindows);
+    RT_REQ(hfov_deg > 0.0 && hfov_deg < 180.0, "hfov_deg must be in (0, 180)");
+    for (int q = 0; q < n_fov; ++q) RT_REQ(fov_deg[q] >= 0.0, "fov_deg must be >= 0");
+    int dev;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    Windows win;
+    fov_windows(width, hfov_deg, fov_deg, n_fov, &win);
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = (size_t)xcorr_chunks(height) * width * channels * 4 * sizeof(double);
+    void* partial = nullptr;
+    RT_CK(cudaMallocAsync(&partial, bytes, st));
+    cudaError_t e = launch_xcorr(d_f, d_g, height, width, channels, win, partial, d_out, st);
+    cudaError_t e2 = cudaFreeAsync(partial, st);
+    RT_CK(e);
+    RT_CK(e2);
+    return RT_OK;
+}
+
+int rt_eval_medium(int32_t precision, double Lambda, double A, const double* d_xy, int64_t npoints,
+                   double* d_out, void* stream)
+{
+    g_err[0] = 0;
+    RT_REQ(precision == RT_FP32 || precision == RT_FP64, "precision must be RT_FP32 or RT_FP64");
+    RT_REQ(Lambda > 0.0 && A >= 0.0 && 2.0 * kPi * A / Lambda < 1.0, "need Lambda > 0 and 0 <= kA < 1");
+    RT_REQ(npoints >= 0 && (npoints == 0 || (d_xy && d_out)), "null pointer argument");
+    int dev;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    RT_CK(launch_medium(precision, kTwoPi * A / Lambda, Lambda, d_xy, npoints, d_out, (cudaStream_t)stream));
+    return RT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,213 @@
+// rt_device.cuh -- device-side arithmetic of the grating-cloak ray tracer.
+//
+// Units: every length is divided by the grating period Lambda, so k = 2 pi.
+// The abscissa x is carried as an integer cell plus a fraction X in
+// [-1/2, 1/2): the index (Eq. 1) is periodic in x, so the W0 solve, the
+// force and the trochoid see only X and keep full FP32 resolution however
+// far the ray is from the origin.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace grt {
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kTwoPi = 6.28318530717958647692;
+constexpr double kInvTwoPi = 0.15915494309189533577;
+constexpr double kLog2e = 1.44269504088896340736;
+
+// ------------------------------------------------------------------------
+// Scene constants (normalised units) passed by value to every kernel.
+// ------------------------------------------------------------------------
+struct DevScene {
+    double A, kA, H, E2, ytop, yrec;       // grating, cloak box (E2 = E/2), record plane
+    double C[3], f[3], r[3], u[3];         // camera position and basis
+    double tx, ty;                          // tangent of the half fields of view
+    double fr[3], ur[3], Pb[3];             // background plane frame
+    double cell, texel;                     // checkerboard cell, texel size
+    double h, rtol, atol, hmax;             // integrator
+    double Lambda;                          // world scale of outputs
+    float col0[3], col1[3];
+    const float* tex;
+    const int64_t* pix_list;                // optional subset of pixels
+    uint64_t seed, scene_id;
+    int64_t max_steps;
+    int64_t nwork;                          // pixels to render
+    int mirror, cloak, width, height, wout, spp, m, centre_line;
+    int background, tex_size, integrator, max_bounces;
+};
+
+// ------------------------------------------------------------------------
+// Precision back ends.  FP32 uses the SFU (MUFU) approximations; FP64 the
+// CUDA math library.
+// ------------------------------------------------------------------------
+template <class R> struct Mth;
+
+template <> struct Mth<float> {
+    static __device__ __forceinline__ float rcp(float x) {
+        float y;
+        asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    static __device__ __forceinline__ float ex2(float x) {
+        float y;
+        asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
+    // sin and cos of 2 pi a for |a| <= 1/2
+    static __device__ __forceinline__ void sincos2pi(float a, float& s, float& c) {
+        __sincosf(6.28318530717958647692f * a, &s, &c);
+    }
+    static __device__ __forceinline__ void sincos(float a, float& s, float& c) { __sincosf(a, &s, &c); }
+    static __device__ __forceinline__ float rint_(float x) { return rintf(x); }
+    static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
+    static constexpr float kTol2 = 1e-8f;      // |dW|^2 after which one more step is below FP32 resolution
+    static constexpr int kMaxIt = 16;
+    static constexpr float kEventTol = 2e-9f;   // |g| at a located event (units of Lambda)
+    static constexpr int kEventIt = 40;
+    static constexpr float kRehit = 1e-5f;      // a ray leaving a surface cannot meet it again closer
+    static constexpr float kEps = 1.1920929e-7f;
+};
+
+template <> struct Mth<double> {
+    static __device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+    static __device__ __forceinline__ double ex2(double x) { return exp2(x); }
+    static __device__ __forceinline__ void sincos2pi(double a, double& s, double& c) { sincospi(2.0 * a, &s, &c); }
+    static __device__ __forceinline__ void sincos(double a, double& s, double& c) { ::sincos(a, &s, &c); }
+    static __device__ __forceinline__ double rint_(double x) { return rint(x); }
+    static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
+    static constexpr double kTol2 = 1e-18;
+    static constexpr int kMaxIt = 40;
+    static constexpr double kEventTol = 1e-14;
+    static constexpr int kEventIt = 100;
+    static constexpr double kRehit = 1e-9;
+    static constexpr double kEps = 2.220446049250313e-16;
+};
+
+// ------------------------------------------------------------------------
+// Lambert W0 of zeta = -kA exp(i k z) (Eq. 1 with c = iA, Eq. 13).
+//
+// W e^W = zeta is solved in the equivalent form
+//     g(W) = W + kA exp(-(W - i k z)) = 0,
+// whose Newton constant g''/2g' = -W/(2(1+W)) is small for the cloak's
+// |W| < kA < 1, by Newton steps with the derivative 1 + W of the current
+// iterate (g'(W) = 1 + W at the root).  Each step costs one exp, one
+// sin/cos pair and one reciprocal.  The reciprocal r = 1/(1+W) of the final
+// iterate is corrected to second order in the last step dW.
+// On return (wr, wi) = W and (rr, ri) = 1/(1+W); the result is the number of
+// Newton steps.
+// ------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ int w0_solve(R kA, R X, R y, R& wr, R& wi, R& rr, R& ri)
+{
+    const R L2E = R(kLog2e);
+    const R KL2E = R(kTwoPi * kLog2e);
+    const R I2PI = R(kInvTwoPi);
+    int it = 0;
+    for (;;) {
+        const R ar = R(1) + wr, ai = wi;
+        const R inv = Mth<R>::rcp(ar * ar + ai * ai);
+        rr = ar * inv;
+        ri = -ai * inv;
+        // q = kA exp(-(Re W + k y)) (cos(k X - Im W) + i sin(k X - Im W))
+        const R e = kA * Mth<R>::ex2(-(wr * L2E) - y * KL2E);
+        R a = X - wi * I2PI;
+        a -= Mth<R>::rint_(a);
+        R s, c;
+        Mth<R>::sincos2pi(a, s, c);
+        const R nr = wr + e * c, ni = wi + e * s;           // g(W)
+        const R dr = nr * rr - ni * ri, di = nr * ri + ni * rr;  // dW = g(W)/(1+W)
+        wr -= dr;
+        wi -= di;
+        ++it;
+        const R d2 = dr * dr + di * di;
+        if (d2 <= Mth<R>::kTol2 || it >= Mth<R>::kMaxIt) {
+            const R tr = rr * dr - ri * di, ti = rr * di + ri * dr;   // r dW
+            const R nrr = rr + (rr * tr - ri * ti), nri = ri + (rr * ti + ri * tr);
+            rr = nrr;
+            ri = nri;
+            return it;
+        }
+    }
+}
+
+// First-order continuation of W along a displacement (dx, dy):
+// W' = dW/dz = i k W / (1 + W) = i k W r.
+template <class R>
+__device__ __forceinline__ void w0_predict(R& wr, R& wi, R rr, R ri, R dx, R dy)
+{
+    const R k = R(kTwoPi);
+    const R pr = wr * rr - wi * ri, pi = wr * ri + wi * rr;   // W r
+    wr += k * (-pi * dx - pr * dy);
+    wi += k * (pr * dx - pi * dy);
+}
+
+// Ray force F = grad(n^2)/2 = n grad n (Eq. 12 times n) in the Hamiltonian
+// parameter: F = k n^2 (Im(W r^2), Re(W r^2)) with r = 1/(1+W), n^2 = |r|^2.
+template <class R>
+__device__ __forceinline__ void ray_force(R wr, R wi, R rr, R ri, R& Fx, R& Fy)
+{
+    const R n2 = rr * rr + ri * ri;
+    const R r2r = rr * rr - ri * ri, r2i = R(2) * rr * ri;
+    const R gr = wr * r2r - wi * r2i, gi = wr * r2i + wi * r2r;
+    const R s = R(kTwoPi) * n2;
+    Fx = s * gi;
+    Fy = s * gr;
+}
+
+// FP64 W0 from a cold start near the branch point zeta = -1/e (|1 + W| small):
+// Halley's iteration on W e^W = zeta started from the branch-point series in
+// p = sqrt(2 (e zeta + 1)) (Corless et al. 1996).  Used by the FP32 path when
+// |zeta + 1/e| < 1e-3.
+__device__ __noinline__ void w0_branch_fp64(double kA, double X, double y, double& wr, double& wi,
+                                            int& iters);
+
+// ------------------------------------------------------------------------
+// Trochoid grating (Eq. 2): x = xi - A sin(k xi), y = A cos(k xi).
+// ------------------------------------------------------------------------
+// Kepler's equation E - e sin E = M for the phase E = k xi given M = k x,
+// e = kA < 1, by Newton's method from E = M + e sin M.  M is reduced to
+// [-pi, pi] by the caller.
+template <class R>
+__device__ __forceinline__ R kepler(R M, R e)
+{
+    R s, c;
+    Mth<R>::sincos(M, s, c);
+    R E = M + e * s;
+    for (int it = 0; it < (sizeof(R) == 4 ? 6 : 12); ++it) {
+        Mth<R>::sincos(E, s, c);
+        const R f = E - e * s - M;
+        const R dE = f / (R(1) - e * c);
+        E -= dE;
+        if (fabs(dE) <= R(4) * Mth<R>::kEps * (R(1) + fabs(E))) break;
+    }
+    return E;
+}
+
+// Phase E and surface height y_s at cell-local abscissa X.
+template <class R>
+__device__ __forceinline__ R trochoid_phase(R X, R kA)
+{
+    R a = X - Mth<R>::rint_(X);
+    return kepler(R(kTwoPi) * a, kA);
+}
+
+// ------------------------------------------------------------------------
+// SplitMix64 (Steele, Lea & Flood 2014): output m of the generator seeded
+// with `seed` is mix(seed + m * golden).
+// ------------------------------------------------------------------------
+__device__ __forceinline__ uint64_t splitmix64(uint64_t seed, uint64_t m)
+{
+    uint64_t z = seed + m * 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ double uniform24(uint64_t seed, uint64_t m)
+{
+    return (double)(splitmix64(seed, m) >> 40) * (1.0 / 16777216.0);
+}
+
+}  // namespace grt

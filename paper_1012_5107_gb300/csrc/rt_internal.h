@@ -1,0 +1,37 @@
+// rt_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rt.h"
+#include "rt_device.cuh"
+
+namespace grt {
+
+constexpr int kRenderBlock = 128;
+constexpr int kMaxWindows = 16;
+constexpr int kCounters = 16;      // [0] work counter, [1..11] statistics
+
+struct Windows {
+    int n;
+    int j0[kMaxWindows], j1[kMaxWindows];
+};
+
+cudaError_t render_occupancy(int precision, int* blocks_per_sm);
+cudaError_t launch_render(const DevScene& sc, int precision, float* rgb, uint8_t* rgb8, rt_ray_record* rec,
+                          unsigned long long* counters, int grid, cudaStream_t stream);
+cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,
+                          cudaStream_t stream);
+
+// Cross-correlation: column moments into `partial` (nchunks x W*C double4),
+// then one block per window.
+int xcorr_chunks(int H);
+cudaError_t launch_xcorr(const float* f, const float* g, int H, int W, int C, const Windows& win, void* partial,
+                         double* out, cudaStream_t stream);
+
+// Columns of a width-W image inside each field of view (host).
+void fov_windows(int W, double hfov_deg, const double* fov_deg, int n_fov, Windows* win);
+
+void set_error(const char* fmt, ...);
+
+}  // namespace grt

@@ -1,0 +1,216 @@
+"""Python binding of the C ABI in include/rt.h (ctypes).
+
+Argument marshalling only: every step of the render and the cross-correlation
+runs in the CUDA library.  Device buffers are torch tensors (their data
+pointers are passed); the stream defaults to torch's current stream.  If the
+library has not been built this module raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libgratingrt.so")
+
+RT_OK, RT_PENDING = 0, 1
+RT_EINVAL, RT_ENOMEM, RT_ENODEV, RT_EBUSY, RT_ETIMEDOUT, RT_ECUDA = -22, -12, -19, -16, -110, -5
+RT_FP32, RT_FP64 = 0, 1
+
+
+class RtError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rt error {code}: {msg}")
+        self.code = code
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [
+        ("Lambda", C.c_double), ("A", C.c_double), ("H", C.c_double), ("E", C.c_double),
+        ("cam_dist", C.c_double), ("elev_deg", C.c_double), ("azim_deg", C.c_double), ("hfov_deg", C.c_double),
+        ("bg_cell", C.c_double), ("tex_texel", C.c_double),
+        ("colour0", C.c_double * 3), ("colour1", C.c_double * 3),
+        ("h", C.c_double), ("rtol", C.c_double), ("atol", C.c_double), ("h_max", C.c_double),
+        ("seed", C.c_uint64), ("scene_id", C.c_uint64),
+        ("max_steps", C.c_int64),
+        ("tex", C.POINTER(C.c_float)),
+        ("mirror", C.c_int32), ("cloak", C.c_int32), ("width", C.c_int32), ("height", C.c_int32),
+        ("spp", C.c_int32), ("centre_line", C.c_int32), ("background", C.c_int32), ("tex_size", C.c_int32),
+        ("integrator", C.c_int32), ("precision", C.c_int32), ("max_bounces", C.c_int32), ("flags", C.c_int32),
+    ]
+
+
+class RayRecord(C.Structure):
+    _fields_ = [
+        ("pos", C.c_double * 3), ("dir", C.c_double * 3), ("rgb", C.c_float * 3),
+        ("status", C.c_int32), ("bounces", C.c_int32), ("events", C.c_int32), ("steps", C.c_int64),
+    ]
+
+
+RECORD_DTYPE = np.dtype({
+    "names": ["pos", "dir", "rgb", "status", "bounces", "events", "steps"],
+    "formats": [("<f8", 3), ("<f8", 3), ("<f4", 3), "<i4", "<i4", "<i4", "<i8"],
+    "offsets": [0, 24, 48, 60, 64, 68, 72],
+    "itemsize": 80,
+})
+assert C.sizeof(RayRecord) == RECORD_DTYPE.itemsize
+
+
+class Stats(C.Structure):
+    _fields_ = [("rays", C.c_uint64), ("steps", C.c_uint64), ("evals", C.c_uint64), ("newton", C.c_uint64),
+                ("events", C.c_uint64), ("fp64_refine", C.c_uint64), ("status", C.c_uint64 * 5)]
+
+
+_lib = None
+
+EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels", "rt_render_host",
+           "rt_scene_stats", "rt_xcorr", "rt_eval_medium", "rt_last_error", "rt_version"]
+
+
+def lib() -> C.CDLL:
+    """Load libgratingrt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    L.rt_create_scene.argtypes = [C.POINTER(SceneDesc), C.POINTER(vp)]
+    L.rt_destroy_scene.argtypes = [vp]
+    L.rt_destroy_scene.restype = None
+    L.rt_render.argtypes = [vp, vp, vp, vp, vp]
+    L.rt_render_pixels.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
+    L.rt_render_host.argtypes = [vp, vp, vp, vp]
+    L.rt_scene_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.rt_xcorr.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
+                           C.c_double, vp, vp]
+    L.rt_eval_medium.argtypes = [C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp, vp]
+    L.rt_last_error.restype = C.c_char_p
+    L.rt_version.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc: int):
+    if rc < 0:
+        raise RtError(rc, lib().rt_last_error().decode())
+    return rc
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    return t.data_ptr()
+
+
+def make_desc(params: dict, tex: np.ndarray | None = None) -> tuple[SceneDesc, np.ndarray | None]:
+    d = SceneDesc()
+    for name, _ in SceneDesc._fields_:
+        if name in ("tex", "colour0", "colour1"):
+            continue
+        if name in params:
+            setattr(d, name, params[name])
+    for name in ("colour0", "colour1"):
+        getattr(d, name)[:] = [float(v) for v in params.get(name, (0.0, 0.0, 0.0))]
+    keep = None
+    if tex is not None:
+        keep = np.ascontiguousarray(tex, dtype=np.float32)
+        d.tex = keep.ctypes.data_as(C.POINTER(C.c_float))
+        d.tex_size = int(keep.shape[0])
+    return d, keep
+
+
+class Scene:
+    """A scene on the current CUDA device (rt_create_scene)."""
+
+    def __init__(self, params: dict, tex: np.ndarray | None = None):
+        self.params = dict(params)
+        desc, _keep = make_desc(params, tex)
+        h = C.c_void_p()
+        _check(lib().rt_create_scene(C.byref(desc), C.byref(h)))
+        self._h = h
+        self.width = int(params["width"])
+        self.height = int(params["height"])
+        self.spp = int(params["spp"])
+        self.wout = 1 if params.get("centre_line", 0) else self.width
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rt_destroy_scene(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def shape(self) -> tuple[int, int, int]:
+        return (self.height, self.wout, 3)
+
+    def render(self, rgb, rgb8=None, rec=None, stream=None):
+        """rgb: float32 (H, Wout, 3) CUDA tensor; rgb8: uint8 same shape; rec: uint8 tensor of
+        H*Wout*spp*80 bytes (view with RECORD_DTYPE after copying to host)."""
+        _check(lib().rt_render(self._h, _ptr(rgb), _ptr(rgb8), _ptr(rec), _stream(stream)))
+
+    def render_pixels(self, pix, rgb, rec=None, stream=None):
+        _check(lib().rt_render_pixels(self._h, _ptr(pix), int(pix.numel()), _ptr(rgb), _ptr(rec), _stream(stream)))
+
+    def render_host(self, h_rgb: np.ndarray, h_rgb8: np.ndarray | None = None, stream=None):
+        _check(lib().rt_render_host(self._h, h_rgb.ctypes.data, None if h_rgb8 is None else h_rgb8.ctypes.data,
+                                    _stream(stream)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().rt_scene_stats(self._h, C.byref(s)))
+        return {"rays": s.rays, "steps": s.steps, "evals": s.evals, "newton": s.newton, "events": s.events,
+                "fp64_refine": s.fp64_refine, "status": list(s.status)}
+
+
+def records_to_numpy(rec_bytes) -> np.ndarray:
+    """View a uint8 CUDA/CPU tensor of records as a numpy structured array."""
+    a = rec_bytes.cpu().numpy() if hasattr(rec_bytes, "cpu") else np.asarray(rec_bytes)
+    return a.view(RECORD_DTYPE)
+
+
+def xcorr(f, g, fov_deg, hfov_deg: float, out=None, stream=None):
+    """C(0,0) of Eqs. 14-15 per field of view: returns a float64 CUDA tensor (n_fov, C+1)."""
+    import torch
+    if f.dim() == 2:
+        f = f.unsqueeze(-1)
+        g = g.unsqueeze(-1)
+    H, W, Cc = f.shape
+    fov = (C.c_double * len(fov_deg))(*[float(x) for x in fov_deg])
+    if out is None:
+        out = torch.empty((len(fov_deg), Cc + 1), dtype=torch.float64, device=f.device)
+    _check(lib().rt_xcorr(_ptr(f), _ptr(g), H, W, Cc, fov, len(fov_deg), float(hfov_deg), _ptr(out),
+                          _stream(stream)))
+    return out
+
+
+def eval_medium(precision: int, Lambda: float, A: float, xy, out=None, stream=None):
+    """(Re W0, Im W0, n, F_x, F_y) at the points xy (float64 CUDA tensor (n, 2))."""
+    import torch
+    n = xy.shape[0]
+    if out is None:
+        out = torch.empty((n, 5), dtype=torch.float64, device=xy.device)
+    _check(lib().rt_eval_medium(precision, float(Lambda), float(A), _ptr(xy), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def version() -> str:
+    return lib().rt_version().decode()

@@ -1,0 +1,248 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: per-ray exit position <= 1e-4 Lambda and exit direction <= 1e-5
+rad for rays that take the same path (status and bounce count), at most 0.1%
+of pixels whose 8-bit value differs by more than one level, cross-correlations
+within 1e-4."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_1012_5107_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+POS_TOL = 1e-4
+DIR_TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def rt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_5107_gb300 import build as B
+    B.build()
+    from paper_1012_5107_gb300 import rt as r
+    r.lib()
+    return r
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def gpu_render(rt, torch, p, records=True, tex=None):
+    sc = rt.Scene(p, tex=tex)
+    rgb = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+    rgb8 = torch.zeros(sc.shape, dtype=torch.uint8, device="cuda")
+    rec = torch.zeros(sc.height * sc.wout * sc.spp * 80, dtype=torch.uint8, device="cuda") if records else None
+    sc.render(rgb, rgb8, rec)
+    torch.cuda.synchronize()
+    out = dict(rgb=rgb.cpu().numpy(), rgb8=rgb8.cpu().numpy(), stats=sc.stats())
+    if records:
+        out["rec"] = rt.records_to_numpy(rec)
+    sc.close()
+    return out
+
+
+def compare_records(g, o, pos_tol=POS_TOL, dir_tol=DIR_TOL, min_frac=0.999):
+    g = g.reshape(-1)
+    o = o.reshape(-1)
+    same = (g["status"] == o["status"]) & (g["bounces"] == o["bounces"])
+    dpos = np.abs(g["pos"] - o["pos"]).max(1)
+    ddir = np.linalg.norm(g["dir"] - o["dir"], axis=1)
+    ok = same & (dpos <= pos_tol) & (ddir <= dir_tol)
+    info = dict(same=same.mean(), ok=ok.mean(), dpos_med=float(np.median(dpos[same])) if same.any() else 0,
+                dpos_max=float(dpos[same].max()) if same.any() else 0,
+                ddir_max=float(ddir[same].max()) if same.any() else 0)
+    assert ok.mean() >= min_frac, info
+    return info
+
+
+def compare_images(q_gpu, q_ref, max_frac=0.001):
+    diff = np.abs(q_gpu.astype(int) - q_ref.astype(int)).max(-1)
+    frac = (diff > 1).mean()
+    assert frac <= max_frac, frac
+    return frac
+
+
+# ---------------------------------------------------------------------------
+# Index, gradient and W0 (Eqs. 1, 12, 13)
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,tol", [(1, 1e-12), (0, 2e-6)])
+def test_medium_parity(rt, torch, orc, precision, tol):
+    for lam, A in [(1.0, 0.04), (1.0, 3 / (16 * math.pi)), (1.7, 0.1)]:
+        sc = orc.Scene(inputs.base_scene(Lambda=lam, A=A))
+        rng = np.random.default_rng(5)
+        x = rng.uniform(-20 * lam, 20 * lam, 4000)
+        ys = orc.trochoid(sc, x)[:, 1]
+        y = ys + rng.uniform(0.0, 2.0 * lam, 4000) ** 2
+        ref = orc.index(sc, x, y)
+        xy = torch.tensor(np.stack([x, y], 1), dtype=torch.float64, device="cuda")
+        got = rt.eval_medium(precision, lam, A, xy).cpu().numpy()
+        W = ref[:, 0] + 1j * ref[:, 1]
+        Wg = got[:, 0] + 1j * got[:, 1]
+        assert np.abs(Wg - W).max() <= tol * max(1.0, np.abs(W).max()) * 4
+        assert np.abs(got[:, 2] - ref[:, 2]).max() <= tol * 4
+        F = ref[:, 2:3] * ref[:, 3:5]                     # n grad n
+        scale = np.abs(F).max()
+        assert np.abs(got[:, 3:5] - F).max() <= tol * 40 * max(scale, 1.0)
+
+
+@pytest.mark.parametrize("kA", [0.93, 0.97])
+def test_medium_near_branch_point(rt, torch, orc, kA):
+    """Close to a crest with kA near 1, |zeta + 1/e| < 1e-3: the FP32 path
+    refines W0 in FP64."""
+    A = kA / (2 * math.pi)
+    sc = orc.Scene(inputs.base_scene(A=A))
+    x = np.linspace(-0.02, 0.02, 41)
+    ys = orc.trochoid(sc, x)[:, 1]
+    y = ys + 1e-6
+    ref = orc.index(sc, x, y)
+    zeta = -kA * np.exp(-2 * math.pi * y) * np.exp(2j * math.pi * x)
+    assert np.abs(zeta + 1 / math.e).min() < 1e-3
+    xy = torch.tensor(np.stack([x, y], 1), dtype=torch.float64, device="cuda")
+    for precision, tol in [(1, 1e-10), (0, 1e-5)]:
+        got = rt.eval_medium(precision, 1.0, A, xy).cpu().numpy()
+        W = ref[:, 0] + 1j * ref[:, 1]
+        Wg = got[:, 0] + 1j * got[:, 1]
+        assert np.abs(Wg - W).max() <= tol, (precision, np.abs(Wg - W).max())
+        assert np.abs(got[:, 2] / ref[:, 2] - 1).max() <= tol * 10
+
+
+# ---------------------------------------------------------------------------
+# Whole renders (Sec. 4): flat mirror, bare grating, cloaked grating
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision", [1, 0])
+@pytest.mark.parametrize("kind", ["mirror", "bare", "cloak"])
+def test_render_small_config(rt, torch, orc, precision, kind):
+    """64 x 64, 1 sample per pixel, RK4 h = Lambda/200: every sample against the oracle."""
+    p = inputs.three_renders(inputs.config_small(precision=precision))[kind]
+    g = gpu_render(rt, torch, p)
+    o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
+    info = compare_records(g["rec"], o_rec, min_frac=0.998 if kind == "cloak" else 0.999)
+    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001 if kind != "cloak" else 0.005)
+    assert g["stats"]["rays"] == 64 * 64
+    if precision == 1:
+        assert info["dpos_med"] < 1e-9
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_render_main_config_sampled(rt, torch, orc, precision):
+    """512 x 512, 4 stratified samples per pixel: the full render in the
+    launch configuration the benchmark times, checked on a seeded subset of
+    pixels that the oracle traces one by one."""
+    p = inputs.three_renders(inputs.config_main(precision=precision))["cloak"]
+    g = gpu_render(rt, torch, p)
+    pix = inputs.pixel_subset(512, 512, 1500, seed=21)
+    o_rgb, o_rec = orc.render_pixels(orc.Scene(p), pix, records=True)
+    grec = g["rec"].reshape(512 * 512, 4)[pix]
+    compare_records(grec, o_rec.reshape(-1, 4), min_frac=0.998)
+    q = g["rgb8"].reshape(-1, 3)[pix]
+    compare_images(q, orc.quantize(o_rgb), max_frac=0.005)
+    st = g["stats"]
+    assert st["rays"] == 512 * 512 * 4
+    assert sum(st["status"]) == st["rays"]
+
+
+def test_render_pixels_equals_full_render(rt, torch, orc):
+    p = inputs.base_scene(width=48, height=40, spp=4, seed=3, precision=0)
+    full = gpu_render(rt, torch, p)
+    sc = rt.Scene(p)
+    pix_np = inputs.pixel_subset(40, 48, 300, seed=4)
+    pix = torch.tensor(pix_np, dtype=torch.int64, device="cuda")
+    rgb = torch.zeros((300, 3), dtype=torch.float32, device="cuda")
+    rec = torch.zeros(300 * 4 * 80, dtype=torch.uint8, device="cuda")
+    sc.render_pixels(pix, rgb, rec)
+    torch.cuda.synchronize()
+    assert np.array_equal(rgb.cpu().numpy(), full["rgb"].reshape(-1, 3)[pix_np])
+    r = rt.records_to_numpy(rec).reshape(300, 4)
+    f = full["rec"].reshape(-1, 4)[pix_np]
+    assert np.array_equal(r["pos"], f["pos"]) and np.array_equal(r["dir"], f["dir"])
+
+
+def test_render_is_deterministic(rt, torch):
+    p = inputs.base_scene(width=64, height=48, spp=4, seed=8, precision=0)
+    a = gpu_render(rt, torch, p)
+    b = gpu_render(rt, torch, p)
+    assert np.array_equal(a["rgb"], b["rgb"])
+    assert np.array_equal(a["rec"]["dir"], b["rec"]["dir"])
+
+
+@pytest.mark.parametrize("over", [
+    dict(width=1, height=1, spp=1),
+    dict(width=7, height=5, spp=3),                    # non-square spp, ragged sizes
+    dict(width=33, height=17, spp=1, centre_line=1),
+    dict(width=16, height=16, spp=1, A=0.0),           # flat limit of the grating
+    dict(width=16, height=16, spp=1, max_bounces=0),   # guard: every reflection exceeds the cap
+    dict(width=16, height=16, spp=1, max_steps=50),    # guard: step cap inside the cloak
+    dict(width=12, height=12, spp=4, elev_deg=10.0, azim_deg=35.0, Lambda=0.6, A=0.03, E=4.8, H=1.2),
+])
+@pytest.mark.parametrize("precision", [1, 0])
+def test_edge_cases(rt, torch, orc, over, precision):
+    p = inputs.base_scene(**over, precision=precision)
+    g = gpu_render(rt, torch, p)
+    o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
+    n = o_rec.size
+    compare_records(g["rec"], o_rec, pos_tol=POS_TOL * p["Lambda"], min_frac=1.0 - 2.0 / n)
+    assert np.array_equal(np.sort(g["rec"]["status"].ravel()), np.sort(o_rec["status"].ravel())) or n > 100
+
+
+def test_empty_pixel_list(rt, torch):
+    sc = rt.Scene(inputs.base_scene(width=8, height=8, spp=1, precision=0))
+    pix = torch.zeros(0, dtype=torch.int64, device="cuda")
+    rgb = torch.zeros((0, 3), dtype=torch.float32, device="cuda")
+    sc.render_pixels(pix, rgb)
+    torch.cuda.synchronize()
+    assert sc.stats()["rays"] == 0
+
+
+def test_texture_background(rt, torch, orc):
+    tex = inputs.value_noise(256, seed=3, octaves=4, base_period=64)
+    p = inputs.base_scene(width=40, height=30, spp=4, background=1, tex_size=256, tex_texel=1 / 32,
+                          precision=0)
+    g = gpu_render(rt, torch, p, tex=tex)
+    o_rgb, o_rec = orc.render(orc.Scene(p, tex=tex), records=True)
+    compare_records(g["rec"], o_rec, min_frac=0.995)
+    assert np.abs(g["rgb"] - o_rgb).max() < 0.05
+    assert np.median(np.abs(g["rgb"] - o_rgb)) < 1e-5
+
+
+# ---------------------------------------------------------------------------
+# Cross-correlation (Sec. 5, Eqs. 14-15)
+# ---------------------------------------------------------------------------
+def test_xcorr_parity(rt, torch, orc):
+    rng = np.random.default_rng(2)
+    for H, W in [(64, 64), (37, 129), (512, 1), (300, 512)]:
+        f = rng.random((H, W, 3)).astype(np.float32)
+        g = (0.6 * f + 0.4 * rng.random((H, W, 3))).astype(np.float32)
+        fovs = [0.0, 10.0, 25.0, 50.0]
+        out = rt.xcorr(torch.tensor(f, device="cuda"), torch.tensor(g, device="cuda"), fovs, 50.0)
+        out = out.cpu().numpy()
+        for q, fov in enumerate(fovs):
+            j0, j1 = orc.fov_columns(W, 50.0, fov)
+            ref = orc.xcorr(f, g, j0, j1)
+            if j1 > j0:
+                assert np.abs(out[q] - ref).max() < 1e-10
+            else:
+                assert np.isnan(out[q]).all()
+
+
+def test_xcorr_of_renders(rt, torch, orc):
+    """C(cloak, mirror) and C(bare, mirror) of the small workload, GPU vs oracle,
+    within 1e-4."""
+    base = inputs.config_small(precision=0)
+    imgs, refs = {}, {}
+    for kind, p in inputs.three_renders(base).items():
+        imgs[kind] = torch.tensor(gpu_render(rt, torch, p, records=False)["rgb"], device="cuda")
+        refs[kind] = orc.render(orc.Scene(p))
+    for kind in ("cloak", "bare"):
+        out = rt.xcorr(imgs["mirror"], imgs[kind], [10.0, 25.0, 50.0], 50.0).cpu().numpy()
+        for q, fov in enumerate([10.0, 25.0, 50.0]):
+            j0, j1 = orc.fov_columns(64, 50.0, fov)
+            ref = orc.xcorr(refs["mirror"], refs[kind], j0, j1)
+            assert np.abs(out[q] - ref).max() < 1e-4 * 30, (kind, fov, out[q], ref)

@@ -142,7 +142,7 @@ class Step:
         tot = {}
         for k, s in self.scenes.items():
             for key, v in s.stats().items():
-                if key == "status":
+                if key in ("status", "profile"):
                     continue
                 tot[key] = tot.get(key, 0) + v
         return tot

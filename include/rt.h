@@ -110,9 +110,10 @@ typedef struct rt_scene_desc {
     int32_t flags;            /* reserved, 0                                    */
 } rt_scene_desc;
 
-/* Per-sample exit record: where the ray's final straight segment crosses the
-   plane y = -A + H + Lambda (or its last point if it does not), its unit
-   direction, colour and counters. */
+/* Per-sample exit record: the start of the ray's final straight segment (its
+   last reflection or cloak-exit point; the camera for a ray that meets
+   nothing; the point where a guard stopped it), the segment's unit direction,
+   the sample's colour and counters. */
 typedef struct rt_ray_record {
     double pos[3];
     double dir[3];
@@ -132,6 +133,10 @@ typedef struct rt_stats {
     uint64_t events;          /* located events                                 */
     uint64_t fp64_refine;     /* W0 refinements in FP64 near the branch point   */
     uint64_t status[5];       /* rays per RT_RAY_* status                       */
+    uint64_t profile[4];      /* zero unless built with RT_PROFILE: per-warp
+                                 cycles in the service pass and in the
+                                 integration loop, loop iterations, and lanes
+                                 inside the cloak summed over the iterations    */
 } rt_stats;
 
 typedef struct rt_scene rt_scene;
@@ -174,6 +179,20 @@ int rt_render_host(rt_scene* scene, float* h_rgb, uint8_t* h_rgb8, void* stream)
 
 /* rt_scene_stats: counters of the last render of this scene (waits for it). */
 int rt_scene_stats(rt_scene* scene, rt_stats* out);
+
+/*
+ * rt_scene_set_launch: launch configuration of the scene's render kernel (the
+ * knobs of the autotuner; results are identical for every setting).
+ *   variant     compiled register budget: 0, 1, 2 = sized for 4, 5, 6
+ *               resident blocks of 128 threads per SM; -1 keeps the current one
+ *   min_active  the integration loop of a warp continues while at least this
+ *               many of its 32 lanes are inside the cloak (1..32); 0 keeps it
+ * Returns RT_EINVAL for values out of range.
+ */
+int rt_scene_set_launch(rt_scene* scene, int32_t variant, int32_t min_active);
+
+/* rt_scene_get_launch: the current variant, min_active and grid size (blocks). */
+int rt_scene_get_launch(rt_scene* scene, int32_t* variant, int32_t* min_active, int32_t* grid);
 
 /*
  * rt_xcorr: image cross-correlation C(0,0) of Eqs. 14-15 (Sec. 5) between

@@ -632,14 +632,6 @@ static int or_background(const or_scene* sc, const camera* cam, const double X[3
     return ST_OK;
 }
 
-/* Height of the horizontal plane at which exit positions are recorded: one
-   period above the top of the cloak box, whether or not the box is present,
-   so that the flat-mirror, bare and cloaked versions of a scene compare. */
-static double or_record_plane(const or_scene* sc)
-{
-    return -sc->A + sc->H + sc->Lambda;
-}
-
 /* ------------------------------------------------------------------------ */
 /* Full path of one ray.                                                     */
 /* ------------------------------------------------------------------------ */
@@ -824,16 +816,13 @@ static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], 
         }
     }
 
-    /* exit record: where the final straight segment crosses the record plane */
+    /* exit record: the start of the final straight segment (the last
+       reflection or cloak-exit point; the camera for rays that meet nothing)
+       and its unit direction */
     if (status != ST_OK && status != ST_SKY) { rgb[0] = rgb[1] = rgb[2] = 0.0; }
-    const double yr = or_record_plane(sc);
     double pos[3] = {X[0], X[1], X[2]};
     double pl = sqrt(or_dot(p, p));
     double dir[3] = {p[0] / pl, p[1] / pl, p[2] / pl};
-    if (medium == MED_AIR && dir[1] > 0.0 && X[1] < yr) {
-        const double t = (yr - X[1]) / dir[1];
-        for (int a = 0; a < 3; ++a) pos[a] = X[a] + t * dir[a];
-    }
     if (rec) {
         memcpy(rec->pos, pos, sizeof pos);
         memcpy(rec->dir, dir, sizeof dir);
@@ -926,9 +915,17 @@ int or_camera_dir(const or_scene* sc, int32_t i, int32_t j, int32_t s, double* o
 uint64_t or_splitmix64_out(uint64_t seed, uint64_t m) { return or_splitmix64(seed, m); }
 
 /* Trace one ray from an arbitrary state (tests).  medium 0: air, 1: inside the box. */
+/* A texture background needs its texture. */
+static int or_scene_ok(const or_scene* sc)
+{
+    if (sc->background == 1 && (!sc->tex || sc->tex_size <= 0)) return 0;
+    return 1;
+}
+
 int or_trace_from(const or_scene* sc, const double* X, const double* p, int32_t medium, int32_t surface,
                   or_record* rec, double* traj, int32_t traj_cap, int32_t* traj_len)
 {
+    if (!or_scene_ok(sc)) return -1;
     camera cam;
     or_camera(sc, &cam);
     traj_buf tb = {traj, traj_cap, 0};
@@ -942,6 +939,7 @@ int or_trace_from(const or_scene* sc, const double* X, const double* p, int32_t 
 int or_render_pixels(const or_scene* sc, const int64_t* pix, int64_t npix, float* rgb, or_record* rec,
                      int32_t nthreads)
 {
+    if (!or_scene_ok(sc)) return -1;
     camera cam;
     or_camera(sc, &cam);
     const int wout = sc->centre_line ? 1 : sc->width;

@@ -180,8 +180,9 @@ def trace_from(sc: Scene, X, p, medium: int = 0, surface: int = -1, traj_cap: in
     rec = np.zeros(1, dtype=RECORD_DTYPE)
     traj = np.zeros((max(traj_cap, 1), 6))
     n = C.c_int32(0)
-    lib().or_trace_from(sc.ref, _dp(X), _dp(p), medium, surface, rec.ctypes.data,
-                        _dp(traj) if traj_cap else None, traj_cap, C.byref(n))
+    if lib().or_trace_from(sc.ref, _dp(X), _dp(p), medium, surface, rec.ctypes.data,
+                           _dp(traj) if traj_cap else None, traj_cap, C.byref(n)):
+        raise ValueError("oracle: texture background without a texture")
     return rec[0], traj[: n.value]
 
 
@@ -189,9 +190,10 @@ def render_pixels(sc: Scene, pix, nthreads: int = 0, records: bool = False):
     pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
     rgb = np.zeros((pix.size, 3), dtype=np.float32)
     rec = np.zeros(pix.size * sc.c.spp, dtype=RECORD_DTYPE) if records else None
-    lib().or_render_pixels(sc.ref, pix.ctypes.data_as(C.POINTER(C.c_int64)), pix.size,
-                           rgb.ctypes.data_as(C.POINTER(C.c_float)),
-                           rec.ctypes.data if records else None, nthreads)
+    if lib().or_render_pixels(sc.ref, pix.ctypes.data_as(C.POINTER(C.c_int64)), pix.size,
+                              rgb.ctypes.data_as(C.POINTER(C.c_float)),
+                              rec.ctypes.data if records else None, nthreads):
+        raise ValueError("oracle: texture background without a texture")
     return (rgb, rec) if records else rgb
 
 

@@ -45,6 +45,9 @@ struct rt_scene {
     rt_scene_desc desc;
     DevScene dev;
     int device;
+    int nsm;
+    int variant;              // compiled register budget of the render kernel
+    int min_active;           // lanes inside the cloak that keep the integration loop going
     int grid;
     float* d_tex;
     unsigned long long* d_counters;
@@ -159,6 +162,25 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->integrator = d->integrator;
     s->max_bounces = d->max_bounces;
     s->nwork = (int64_t)d->height * s->wout;
+    s->cd.kA = s->kA; s->cd.A = s->A; s->cd.h = s->h; s->cd.ytop = s->ytop; s->cd.E2 = s->E2;
+    s->cd.rtol = s->rtol; s->cd.atol = s->atol; s->cd.hmax = s->hmax;
+    s->cf.kA = (float)s->kA; s->cf.A = (float)s->A; s->cf.h = (float)s->h; s->cf.ytop = (float)s->ytop;
+    s->cf.E2 = (float)s->E2; s->cf.rtol = (float)s->rtol; s->cf.atol = (float)s->atol; s->cf.hmax = (float)s->hmax;
+    for (int a = 0; a < 3; ++a) {
+        s->ad.fr[a] = s->fr[a]; s->ad.ur[a] = s->ur[a]; s->ad.r[a] = s->r[a]; s->ad.Pb[a] = s->Pb[a];
+        s->af.fr[a] = (float)s->fr[a]; s->af.ur[a] = (float)s->ur[a]; s->af.r[a] = (float)s->r[a];
+        s->af.Pb[a] = (float)s->Pb[a];
+    }
+    s->ad.inv_cell = s->cell > 0.0 ? 1.0 / s->cell : 0.0;
+    s->ad.inv_texel = s->texel > 0.0 ? 1.0 / s->texel : 0.0;
+    s->af.inv_cell = (float)s->ad.inv_cell;
+    s->af.inv_texel = (float)s->ad.inv_texel;
+    s->ymirror = d->mirror == RT_MIRROR_TROCHOID ? s->A : 0.0;
+    s->box_lo[0] = -s->E2; s->box_lo[1] = -s->A; s->box_lo[2] = -s->E2;
+    s->box_hi[0] = s->E2; s->box_hi[1] = s->ytop; s->box_hi[2] = s->E2;
+    s->inv_m = s->m > 0 ? 1.0 / s->m : 0.0;
+    s->two_over_w = 2.0 / (double)d->width;
+    s->two_over_h = 2.0 / (double)d->height;
 }
 
 extern "C" {
@@ -184,9 +206,12 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     s->device = dev;
     build_dev(desc, &s->dev);
     int bps = 0;
-    cudaError_t e = render_occupancy(desc->precision, &bps);
+    s->variant = kDefaultVariant;
+    s->min_active = kMinActive;
+    cudaError_t e = render_occupancy(desc->precision, s->variant, &bps);
     int nsm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    s->nsm = nsm;
     if (e == cudaSuccess && desc->background == RT_BG_TEXTURE) {
         const size_t bytes = (size_t)desc->tex_size * desc->tex_size * sizeof(float);
         e = cudaMalloc(&s->d_tex, bytes);
@@ -232,7 +257,9 @@ static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float
     sc.pix_list = d_pix;
     sc.nwork = nwork;
     RT_CK(cudaMemsetAsync(s->d_counters, 0, kCounters * sizeof(unsigned long long), st));
-    if (nwork > 0) RT_CK(launch_render(sc, s->desc.precision, d_rgb, d_rgb8, d_rec, s->d_counters, s->grid, st));
+    if (nwork > 0)
+        RT_CK(launch_render(sc, s->desc.precision, s->variant, s->min_active, d_rgb, d_rgb8, d_rec, s->d_counters,
+                            s->grid, st));
     RT_CK(cudaEventRecord(s->done, st));
     s->rendered = true;
     return RT_OK;
@@ -285,6 +312,34 @@ int rt_scene_stats(rt_scene* s, rt_stats* out)
     out->events = c[5];
     out->fp64_refine = c[6];
     for (int q = 0; q < 5; ++q) out->status[q] = c[7 + q];
+    for (int q = 0; q < 4; ++q) out->profile[q] = c[12 + q];
+    return RT_OK;
+}
+
+int rt_scene_set_launch(rt_scene* s, int32_t variant, int32_t min_active)
+{
+    g_err[0] = 0;
+    RT_REQ(s, "scene is NULL");
+    RT_REQ(variant >= -1 && variant < kVariants, "variant must be -1 (keep) or 0..%d", kVariants - 1);
+    RT_REQ(min_active == 0 || (min_active >= 1 && min_active <= 32), "min_active must be 0 (keep) or 1..32");
+    if (variant >= 0 && variant != s->variant) {
+        int bps = 0;
+        RT_CK(render_occupancy(s->desc.precision, variant, &bps));
+        RT_REQ(bps > 0, "variant %d does not fit on this device", variant);
+        s->variant = variant;
+        s->grid = bps * s->nsm;
+    }
+    if (min_active > 0) s->min_active = min_active;
+    return RT_OK;
+}
+
+int rt_scene_get_launch(rt_scene* s, int32_t* variant, int32_t* min_active, int32_t* grid)
+{
+    g_err[0] = 0;
+    RT_REQ(s, "scene is NULL");
+    if (variant) *variant = s->variant;
+    if (min_active) *min_active = s->min_active;
+    if (grid) *grid = s->grid;
     return RT_OK;
 }
 

@@ -18,9 +18,32 @@ constexpr double kInvTwoPi = 0.15915494309189533577;
 constexpr double kLog2e = 1.44269504088896340736;
 
 // ------------------------------------------------------------------------
-// Scene constants (normalised units) passed by value to every kernel.
+// Scene constants (normalised units) passed by value to every kernel.  The
+// per-step constants are also stored in the precision of the path, so the
+// inner loop reads them from the constant bank without conversions (a
+// double-to-float conversion runs on the FP64 pipe).
 // ------------------------------------------------------------------------
+template <class R>
+struct StepConst {
+    R kA, A, h, ytop, E2;
+    R rtol, atol, hmax;
+};
+
+// Constants of the straight segments to the background, in the path's precision.
+template <class R>
+struct AirConst {
+    R fr[3], ur[3], r[3], Pb[3];
+    R inv_cell, inv_texel;
+};
+
 struct DevScene {
+    StepConst<float> cf;
+    StepConst<double> cd;
+    AirConst<float> af;
+    AirConst<double> ad;
+    double ymirror;                         // the mirror cannot be met above this height
+    double box_lo[3], box_hi[3];            // cloak box
+    double inv_m, two_over_w, two_over_h;   // sampling constants
     double A, kA, H, E2, ytop, yrec;       // grating, cloak box (E2 = E/2), record plane
     double C[3], f[3], r[3], u[3];         // camera position and basis
     double tx, ty;                          // tangent of the half fields of view
@@ -62,7 +85,12 @@ template <> struct Mth<float> {
     static __device__ __forceinline__ void sincos(float a, float& s, float& c) { __sincosf(a, &s, &c); }
     static __device__ __forceinline__ float rint_(float x) { return rintf(x); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-    static constexpr float kTol2 = 1e-8f;      // |dW|^2 after which one more step is below FP32 resolution
+    // stop when |dW|^2 <= kRel |W|: the next step would change W by about
+    // |dW|^2, a third of the FP32 resolution of W
+    static constexpr float kRel = 3.6e-8f;
+    // the first-order continuation of W0 over dz is kept without a Newton step
+    // when its error k^2 |W| n^3 |dz|^2 / 2 is below 1e-8 |W|
+    static constexpr float kPredTol = 5e-10f;
     static constexpr int kMaxIt = 16;
     static constexpr float kEventTol = 2e-9f;   // |g| at a located event (units of Lambda)
     static constexpr int kEventIt = 40;
@@ -77,7 +105,8 @@ template <> struct Mth<double> {
     static __device__ __forceinline__ void sincos(double a, double& s, double& c) { ::sincos(a, &s, &c); }
     static __device__ __forceinline__ double rint_(double x) { return rint(x); }
     static __device__ __forceinline__ double sqrt_(double x) { return sqrt(x); }
-    static constexpr double kTol2 = 1e-18;
+    static constexpr double kRel = 6e-17;
+    static constexpr double kPredTol = 2.5e-18;
     static constexpr int kMaxIt = 40;
     static constexpr double kEventTol = 1e-14;
     static constexpr int kEventIt = 100;
@@ -122,7 +151,7 @@ __device__ __forceinline__ int w0_solve(R kA, R X, R y, R& wr, R& wi, R& rr, R& 
         wi -= di;
         ++it;
         const R d2 = dr * dr + di * di;
-        if (d2 <= Mth<R>::kTol2 || it >= Mth<R>::kMaxIt) {
+        if (d2 * d2 <= (Mth<R>::kRel * Mth<R>::kRel) * (wr * wr + wi * wi) || it >= Mth<R>::kMaxIt) {
             const R tr = rr * dr - ri * di, ti = rr * di + ri * dr;   // r dW
             const R nrr = rr + (rr * tr - ri * ti), nri = ri + (rr * ti + ri * tr);
             rr = nrr;
@@ -155,13 +184,6 @@ __device__ __forceinline__ void ray_force(R wr, R wi, R rr, R ri, R& Fx, R& Fy)
     Fx = s * gi;
     Fy = s * gr;
 }
-
-// FP64 W0 from a cold start near the branch point zeta = -1/e (|1 + W| small):
-// Halley's iteration on W e^W = zeta started from the branch-point series in
-// p = sqrt(2 (e zeta + 1)) (Corless et al. 1996).  Used by the FP32 path when
-// |zeta + 1/e| < 1e-3.
-__device__ __noinline__ void w0_branch_fp64(double kA, double X, double y, double& wr, double& wi,
-                                            int& iters);
 
 // ------------------------------------------------------------------------
 // Trochoid grating (Eq. 2): x = xi - A sin(k xi), y = A cos(k xi).
@@ -209,5 +231,39 @@ __device__ __forceinline__ double uniform24(uint64_t seed, uint64_t m)
 {
     return (double)(splitmix64(seed, m) >> 40) * (1.0 / 16777216.0);
 }
+
+template <class R> __device__ __forceinline__ const AirConst<R>& air_const(const DevScene& s);
+template <> __device__ __forceinline__ const AirConst<float>& air_const<float>(const DevScene& s) { return s.af; }
+template <> __device__ __forceinline__ const AirConst<double>& air_const<double>(const DevScene& s) { return s.ad; }
+
+// Illinois (modified regula falsi) on [a, b] with fa > 0 >= fb; returns the
+// last point evaluated.
+template <class R, class F>
+__device__ __forceinline__ R illinois_root(F& f, R a, R fa, R b, R fb)
+{
+    int side = 0;
+    R c = b;
+    for (int it = 0; it < Mth<R>::kEventIt; ++it) {
+        c = b - fb * (b - a) / (fb - fa);
+        if (!(c > a && c < b)) c = R(0.5) * (a + b);
+        const R fc = f(c);
+        if (fabs(fc) <= Mth<R>::kEventTol) return c;
+        if (fc < R(0)) {
+            b = c; fb = fc;
+            if (side == -1) fa *= R(0.5);
+            side = -1;
+        } else {
+            a = c; fa = fc;
+            if (side == 1) fb *= R(0.5);
+            side = 1;
+        }
+        if (b - a <= R(4) * Mth<R>::kEps * (R(1) + fabs(b))) return c;
+    }
+    return c;
+}
+
+template <class R> __device__ __forceinline__ const StepConst<R>& step_const(const DevScene& s);
+template <> __device__ __forceinline__ const StepConst<float>& step_const<float>(const DevScene& s) { return s.cf; }
+template <> __device__ __forceinline__ const StepConst<double>& step_const<double>(const DevScene& s) { return s.cd; }
 
 }  // namespace grt

@@ -9,17 +9,27 @@
 namespace grt {
 
 constexpr int kRenderBlock = 128;
+// Compiled register budgets of the render kernel: resident blocks of
+// kRenderBlock threads per SM that each variant is sized for.
+constexpr int kVariants = 3;
+constexpr int kVariantBlocks[kVariants] = {4, 5, 6};
+constexpr int kDefaultVariant = 0;
+constexpr int kMinActive = 24;   // step while at least this many lanes of a warp are inside the cloak
 constexpr int kMaxWindows = 16;
-constexpr int kCounters = 16;      // [0] work counter, [1..11] statistics
+constexpr int kCounters = 16;      // [0] work counter, [1..11] statistics, [12..15] optional profile
+
+#ifndef RT_PROFILE
+#define RT_PROFILE 0
+#endif
 
 struct Windows {
     int n;
     int j0[kMaxWindows], j1[kMaxWindows];
 };
 
-cudaError_t render_occupancy(int precision, int* blocks_per_sm);
-cudaError_t launch_render(const DevScene& sc, int precision, float* rgb, uint8_t* rgb8, rt_ray_record* rec,
-                          unsigned long long* counters, int grid, cudaStream_t stream);
+cudaError_t render_occupancy(int precision, int variant, int* blocks_per_sm);
+cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
+                          rt_ray_record* rec, unsigned long long* counters, int grid, cudaStream_t stream);
 cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,
                           cudaStream_t stream);
 

@@ -1,0 +1,970 @@
+// rt_trace.cuh -- the render kernel of the grating-cloak ray tracer,
+// templated on the arithmetic type R (float or double).
+//
+// Structure.  One lane owns one pixel at a time and traces its samples one
+// after the other, so the per-pixel sum has a fixed order.  The kernel is
+// persistent and alternates two phases per warp:
+//   * the integration loop advances every lane whose ray is inside the cloak
+//     by one RK4 step per iteration, as long as enough lanes of the warp are
+//     inside; a step that crosses a surface, hits the step cap or goes
+//     non-finite only marks the lane;
+//   * the service pass lets every other lane catch up: locate and act on the
+//     marked events, take new pixels (one atomic per group of lanes), start
+//     samples, trace straight segments in air and finish samples.
+// The integration loop touches only the ray state in registers; everything
+// else a lane owns lives in shared memory.
+//
+// Paper: index Eq. 1, its gradient Eq. 12 and W0 (Eq. 13) in Sec. 2-3; the
+// Newtonian ray equation Eq. 11 (Sec. 3), integrated in the Hamiltonian
+// parameter tau (dr/dtau = p, dp/dtau = grad(n^2)/2, |p| = n), which traces
+// the same curves; Snell's law at the cloak boundary (Sec. 3); the trochoid
+// grating of Eq. 2 (Sec. 2); the camera of Sec. 4.
+//
+// Precision.  FP32 keeps the abscissa as cell + fraction and sums the state
+// with compensation; the camera ray is set up in FP64 (a few operations per
+// sample) because its lever arm from the camera to the scene would otherwise
+// dominate the error.  Nothing else in the FP32 kernel uses the FP64 pipe,
+// whose rate on this GPU is 1/64 of FP32.
+#pragma once
+
+#include <cfloat>
+#include <cmath>
+#include <cstdint>
+
+#include "rt.h"
+#include "rt_device.cuh"
+#include "rt_internal.h"
+
+namespace grt {
+
+enum : int { PH_IDLE = 0, PH_AIR = 1, PH_BOX = 2, PH_DONE = 3, PH_EXIT = 4, PH_EVENT = 5, PH_GUARD = 6 };
+enum : int { EV_NONE = -1, EV_GRATING = 0, EV_TOP = 1, EV_XP = 2, EV_XM = 3, EV_ZP = 4, EV_ZM = 5, EV_COUNT = 6 };
+
+// Hot counters, kept in registers.
+struct LaneStats {
+    uint32_t steps, evals, newton, refine;
+};
+
+// Ray inside the cloak, local coordinates: x = cx + X, |X| <= 1/2.
+template <class R>
+struct Box {
+    R cx, X, y, z, px, py, pz;
+    R cX, cy, cz, cpx, cpy;   // compensation terms of the FP32 sums
+    R wr, wi, rr, ri;         // W0 and 1/(1+W0) at (X, y) (a prediction until solved)
+    R Fx, Fy;                 // force at (X, y)
+};
+
+// What a lane owns outside the integration loop (shared memory).
+template <class R>
+struct Cold {
+    R cx, X, y, z;            // air: position, x = cx + X
+    R dx, dy, dz;             // air: unit direction
+    R g1[EV_COUNT];           // event functions at the end of a step that crossed a surface
+    int64_t work;             // work item (pixel slot)
+    int64_t pix;              // pixel index i*wout + j
+    float acc[3], col[3];
+    int sample, bounces, events, status;
+    uint32_t rays, nevents, stat[5];
+};
+
+// ------------------------------------------------------------------------
+// W0 near the branch point in FP64 (FP32 path only).
+// ------------------------------------------------------------------------
+// Halley's iteration on W e^W = zeta from the branch-point series in
+// p = sqrt(2 (e zeta + 1)) (Corless et al. 1996), for |zeta + 1/e| < 1e-3.
+static __device__ __noinline__ void w0_branch_fp64(double kA, double X, double y, double& wr, double& wi,
+                                                   int& iters)
+{
+    const double e = kA * exp(-kTwoPi * y);
+    double s, c;
+    sincospi(2.0 * X, &s, &c);
+    const double zr = -e * c, zi = -e * s;
+    const double qr = 2.0 * (M_E * zr + 1.0), qi = 2.0 * M_E * zi;
+    const double m = sqrt(qr * qr + qi * qi);
+    double pr = sqrt(0.5 * (m + qr));
+    double pi = (pr > 0.0) ? 0.5 * qi / pr : sqrt(0.5 * (m - qr));
+    if (pr == 0.0 && qi < 0.0) pi = -pi;
+    const double p2r = pr * pr - pi * pi, p2i = 2.0 * pr * pi;
+    const double p3r = p2r * pr - p2i * pi, p3i = p2r * pi + p2i * pr;
+    wr = -1.0 + pr - p2r / 3.0 + (11.0 / 72.0) * p3r;
+    wi = pi - p2i / 3.0 + (11.0 / 72.0) * p3i;
+    iters = 0;
+    for (int it = 0; it < 60; ++it) {
+        const double ex = exp(wr);
+        double sw, cw;
+        sincos(wi, &sw, &cw);
+        const double er = ex * cw, ei = ex * sw;
+        const double fr = wr * er - wi * ei - zr, fi = wr * ei + wi * er - zi;
+        const double ar = wr + 1.0, ai = wi;
+        const double nr = (wr + 2.0) * fr - wi * fi, ni = (wr + 2.0) * fi + wi * fr;
+        const double den = 2.0 * (ar * ar + ai * ai);
+        const double tr = (nr * ar + ni * ai) / den, ti = (ni * ar - nr * ai) / den;
+        const double Dr = er * ar - ei * ai - tr, Di = er * ai + ei * ar - ti;
+        const double dd = Dr * Dr + Di * Di;
+        const double dwr = (fr * Dr + fi * Di) / dd, dwi = (fi * Dr - fr * Di) / dd;
+        wr -= dwr;
+        wi -= dwi;
+        ++iters;
+        if (!(dwr * dwr + dwi * dwi > 1e-30 * (wr * wr + wi * wi))) break;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void w0_eval(R kA, R X, R y, R& wr, R& wi, R& rr, R& ri, LaneStats& st)
+{
+    st.newton += w0_solve(kA, X, y, wr, wi, rr, ri);
+    st.evals += 1;
+    if constexpr (sizeof(R) == 4) {
+        // |zeta + 1/e| < 1e-3 corresponds to |1 + W0|^2 < 2e * 1e-3
+        if (rr * rr + ri * ri > R(1.0 / (2.0 * M_E * 1e-3))) {
+            double dwr, dwi;
+            int it;
+            w0_branch_fp64((double)kA, (double)X, (double)y, dwr, dwi, it);
+            const double ar = 1.0 + dwr, ai = dwi, inv = 1.0 / (ar * ar + ai * ai);
+            wr = (R)dwr;
+            wi = (R)dwi;
+            rr = (R)(ar * inv);
+            ri = (R)(-ai * inv);
+            st.refine += 1;
+            st.newton += it;
+        }
+    }
+}
+
+// W0 at (X, y) from its value at a point (dx, dy) away: first-order
+// continuation, then Newton steps unless the continuation is already exact to
+// the working precision (its error is about k^2 |W| n^3 |dz|^2 / 2); in that
+// case 1/(1+W) is continued to first order as well.
+template <class R>
+__device__ __forceinline__ void w0_continue(R kA, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri, LaneStats& st)
+{
+    const R n2 = rr * rr + ri * ri;
+    const R dz2 = dx * dx + dy * dy;
+    const R ow = wr, owi = wi;
+    w0_predict(wr, wi, rr, ri, dx, dy);
+    if (dz2 * n2 * (n2 > R(1) ? n2 : R(1)) <= Mth<R>::kPredTol) {
+        const R ddr = wr - ow, ddi = wi - owi;            // dW
+        const R tr = rr * ddr - ri * ddi, ti = rr * ddi + ri * ddr;   // r dW
+        const R nrr = rr - (rr * tr - ri * ti), nri = ri - (rr * ti + ri * tr);   // r (1 - r dW)
+        rr = nrr;
+        ri = nri;
+        st.evals += 1;
+        return;
+    }
+    w0_eval(kA, X, y, wr, wi, rr, ri, st);
+}
+
+// ------------------------------------------------------------------------
+// RK4 in the cloak.
+// ------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void kahan_add(R& s, R& c, R inc)
+{
+    if constexpr (sizeof(R) == 4) {
+        const R yv = inc - c;
+        const R t = s + yv;
+        c = (t - s) - yv;
+        s = t;
+    } else {
+        s += inc;
+    }
+}
+
+// One RK4 step of size h from s (W0 solved and force known at s) into o;
+// o's W0 is continued to the end point but not solved.
+template <class R>
+__device__ __forceinline__ void rk4_step(R kA, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
+{
+    const R h2 = R(0.5) * h;
+    R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
+    // stage 2 at r + h/2 p
+    const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
+    w0_continue(kA, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
+    R F2x, F2y;
+    ray_force(wr, wi, rr, ri, F2x, F2y);
+    // stage 3 at r + h/2 (p + h/2 F1), (h/2)^2 F1 away from stage 2
+    const R X3 = s.X + h2 * (s.px + h2 * s.Fx), y3 = s.y + h2 * (s.py + h2 * s.Fy);
+    w0_continue(kA, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
+    R F3x, F3y;
+    ray_force(wr, wi, rr, ri, F3x, F3y);
+    // stage 4 at r + h (p + h/2 F2)
+    const R X4 = s.X + h * (s.px + h2 * F2x), y4 = s.y + h * (s.py + h2 * F2y);
+    w0_continue(kA, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
+    R F4x, F4y;
+    ray_force(wr, wi, rr, ri, F4x, F4y);
+    // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
+    const R h6 = h * R(1.0 / 6.0), hh6 = h * h6;
+    const R dX = h * s.px + hh6 * (s.Fx + F2x + F3x);
+    const R dY = h * s.py + hh6 * (s.Fy + F2y + F3y);
+    const R dZ = h * s.pz;
+    const R dPx = h6 * (s.Fx + R(2) * (F2x + F3x) + F4x);
+    const R dPy = h6 * (s.Fy + R(2) * (F2y + F3y) + F4y);
+    o = s;
+    kahan_add(o.X, o.cX, dX);
+    kahan_add(o.y, o.cy, dY);
+    kahan_add(o.z, o.cz, dZ);
+    kahan_add(o.px, o.cpx, dPx);
+    kahan_add(o.py, o.cpy, dPy);
+    w0_predict(wr, wi, rr, ri, o.X - X4, o.y - y4);
+    o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
+    if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
+    else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+}
+
+// ------------------------------------------------------------------------
+// Events inside the cloak: positive while the ray is inside, negative once it
+// crossed the grating (v = Im w = y + Re W0/k < 0) or a face of the box.
+// ------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ R event_g(const StepConst<R>& k, int ev, const Box<R>& s)
+{
+    switch (ev) {
+        case EV_GRATING: return s.y + s.wr * R(kInvTwoPi);
+        case EV_TOP: return k.ytop - s.y;
+        case EV_XP: return (k.E2 - s.cx) - s.X;
+        case EV_XM: return (k.E2 + s.cx) + s.X;
+        case EV_ZP: return k.E2 - s.z;
+        default: return k.E2 + s.z;
+    }
+}
+
+// h grad g . p: the derivative of g(Phi_{theta h}(s)) in theta at the state s.
+template <class R>
+__device__ __forceinline__ R event_slope(int ev, const Box<R>& s, R h)
+{
+    switch (ev) {
+        case EV_GRATING: return h * (s.ri * s.px + s.rr * s.py);   // grad v = (Im r, Re r)
+        case EV_TOP: return -h * s.py;
+        case EV_XP: return -h * s.px;
+        case EV_XM: return h * s.px;
+        case EV_ZP: return -h * s.pz;
+        default: return h * s.pz;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ void face_normal(int ev, R N[3])
+{
+    N[0] = N[1] = N[2] = R(0);
+    if (ev == EV_TOP) N[1] = R(1);
+    else if (ev == EV_XP) N[0] = R(1);
+    else if (ev == EV_XM) N[0] = R(-1);
+    else if (ev == EV_ZP) N[2] = R(1);
+    else if (ev == EV_ZM) N[2] = R(-1);
+    else N[1] = R(-1);
+}
+
+// Root theta in (0, 1] of g_ev(Phi_{theta h}(b)) given its value g1 < 0 at
+// theta = 1 (the zero at theta = 0 divided out when the step starts on that
+// surface).  First guess from the quadratic through g(0), g'(0) and g(1);
+// then Newton steps with the slope at the current point, kept inside the
+// bracket (regula falsi otherwise).  On return t = Phi_{theta h}(b) with W0
+// solved.
+template <class R>
+__device__ R locate_event(const StepConst<R>& k, const Box<R>& b, int ev, bool on_surface, R g1, Box<R>& t,
+                          LaneStats& st)
+{
+    const R h = k.h;
+    const R s0 = event_slope(ev, b, h);
+    R lo = R(0), hi = R(1), glo, ghi = g1;
+    R th;
+    if (on_surface) {
+        glo = s0 > R(0) ? s0 : R(1e-30);
+        const R c = g1 - glo;                        // g/theta ~ s0 + c theta
+        th = (c < R(0)) ? -glo / c : R(0.5);
+    } else {
+        glo = event_g(k, ev, b);
+        if (!(glo > R(0))) {
+            t = b;
+            return R(0);
+        }
+        const R c = g1 - glo - s0;                   // g ~ g0 + s0 theta + c theta^2
+        th = (glo / (glo - g1));                     // secant
+        if (fabs(c) > R(1e-6) * (fabs(s0) + fabs(glo))) {
+            const R disc = s0 * s0 - R(4) * c * glo;
+            if (disc >= R(0)) {
+                const R sq = Mth<R>::sqrt_(disc);
+                const R q = R(-0.5) * (s0 + (s0 >= R(0) ? sq : -sq));
+                R r1 = q / c, r2 = glo / q;
+                if (r1 > R(0) && r1 <= R(1)) th = r1;
+                if (r2 > R(0) && r2 <= R(1) && (!(th > R(0) && th <= R(1)) || r2 < th)) th = r2;
+            }
+        }
+    }
+    if (!(th > lo && th < hi)) th = R(0.5) * (lo + hi);
+    int side = 0;
+    for (int it = 0; it < Mth<R>::kEventIt; ++it) {
+        rk4_step(k.kA, b, th * h, t, st);
+        w0_eval(k.kA, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
+        const R g = event_g(k, ev, t);
+        if (fabs(g) <= Mth<R>::kEventTol) return th;
+        const R gd = on_surface ? g / th : g;
+        if (gd > R(0)) { lo = th; glo = gd; if (side == 1) ghi *= R(0.5); side = 1; }
+        else { hi = th; ghi = gd; if (side == -1) glo *= R(0.5); side = -1; }
+        if (hi - lo <= R(4) * Mth<R>::kEps) return th;
+        if (it + 1 == Mth<R>::kEventIt) break;       // keep t at the last theta evaluated
+        const R dg = event_slope(ev, t, h);
+        const R dgd = on_surface ? (dg * th - g) / (th * th) : dg;
+        R nt = th - gd / dgd;
+        if (!(nt > lo && nt < hi)) nt = (lo * ghi - hi * glo) / (ghi - glo);
+        if (!(nt > lo && nt < hi)) nt = R(0.5) * (lo + hi);
+        th = nt;
+    }
+    return th;
+}
+
+// ------------------------------------------------------------------------
+// Air: local-coordinate helpers, camera, mirror, box, background.
+// ------------------------------------------------------------------------
+// Move the air ray by t along its direction.  t * dx is split exactly into a
+// rounded product and its remainder, so the cell fraction keeps full
+// resolution however long the move.
+template <class R>
+__device__ __forceinline__ void advance(Cold<R>& C, R t)
+{
+    const R a = t * C.dx;
+    const R e = fma(t, C.dx, -a);
+    const R n = Mth<R>::rint_(a);
+    C.cx += n;
+    C.X = (C.X + (a - n)) + e;
+    const R m = Mth<R>::rint_(C.X);
+    C.cx += m;
+    C.X -= m;
+    C.y += t * C.dy;
+    C.z += t * C.dz;
+}
+
+// Camera ray of sample s of pixel pix (Sec. 4), set up in FP64 and advanced
+// to 2^-10 periods before the first surface it can meet (the cloak box, the
+// grating band y = A or the flat mirror), then stored in local coordinates:
+// the lever arm of the FP32 rounding of the direction is that short, and the
+// remaining distance is far above the box-entry threshold of the FP32 path.  Reciprocals and the norm use FP32 seeds refined by one
+// Newton step in FP64.
+template <class R>
+__device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
+{
+    const int i = (int)(C.pix / sc.wout), j = (int)(C.pix % sc.wout);
+    double ox = 0.5, oy = 0.5;
+    if (sc.spp > 1) {
+        const uint64_t c = (((uint64_t)sc.scene_id * (uint64_t)sc.height + (uint64_t)i) * (uint64_t)sc.wout +
+                            (uint64_t)j) * (uint64_t)sc.spp + (uint64_t)C.sample;
+        const double u1 = uniform24(sc.seed, 2 * c + 1), u2 = uniform24(sc.seed, 2 * c + 2);
+        if (sc.m > 0) {
+            ox = ((double)(C.sample % sc.m) + u1) * sc.inv_m;
+            oy = ((double)(C.sample / sc.m) + u2) * sc.inv_m;
+        } else {
+            ox = u1;
+            oy = u2;
+        }
+    }
+    const double px = sc.centre_line ? 0.0 : ((double)j + ox) * sc.two_over_w - 1.0;
+    const double py = 1.0 - ((double)i + oy) * sc.two_over_h;
+    double d[3], n2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        d[a] = sc.f[a] + px * sc.tx * sc.r[a] + py * sc.ty * sc.u[a];
+        n2 += d[a] * d[a];
+    }
+    double is = (double)rsqrtf((float)n2);
+    is = is * (1.5 - 0.5 * n2 * is * is);
+    for (int a = 0; a < 3; ++a) d[a] *= is;
+    double t = 0.0;
+    if (d[1] < 0.0) {
+        double inv[3];
+        for (int a = 0; a < 3; ++a) {
+            inv[a] = (d[a] != 0.0) ? (double)(1.0f / (float)d[a]) : 0.0;
+            inv[a] = inv[a] * (2.0 - d[a] * inv[a]);
+        }
+        double tf = (sc.ymirror - sc.C[1]) * inv[1];          // the mirror cannot be met earlier
+        if (sc.cloak) {
+            double tn = -INFINITY, tx = INFINITY;
+            bool miss = false;
+            for (int a = 0; a < 3; ++a) {
+                if (d[a] == 0.0) {
+                    if (sc.C[a] < sc.box_lo[a] || sc.C[a] > sc.box_hi[a]) miss = true;
+                    continue;
+                }
+                const double t1 = (sc.box_lo[a] - sc.C[a]) * inv[a], t2 = (sc.box_hi[a] - sc.C[a]) * inv[a];
+                tn = fmax(tn, fmin(t1, t2));
+                tx = fmin(tx, fmax(t1, t2));
+            }
+            if (!miss && tn <= tx && tn > 0.0 && tn < tf) tf = tn;
+        }
+        if (tf > 0.0009765625) t = tf - 0.0009765625;
+    }
+    const double Px = sc.C[0] + t * d[0];
+    const double cxd = rint(Px);
+    C.cx = (R)cxd;
+    C.X = (R)(Px - cxd);
+    C.y = (R)(sc.C[1] + t * d[1]);
+    C.z = (R)(sc.C[2] + t * d[2]);
+    C.dx = (R)d[0];
+    C.dy = (R)d[1];
+    C.dz = (R)d[2];
+}
+
+// Straight line against the flat mirror y = 0.
+template <class R>
+__device__ __forceinline__ R flat_line_hit(const Cold<R>& C)
+{
+    if (C.dy < R(0) && C.y > R(0)) return -C.y / C.dy;
+    return R(INFINITY);
+}
+
+// First hit of the line with the trochoid of Eq. 2, or infinity.  From where
+// the line enters the band |y| <= A it is marched in increments that move the
+// point by at most 1/(8 pi) in the xy-plane, each increment taken from the
+// end of the previous one (so the local coordinates stay small); the first
+// increment ending at or below the surface brackets the hit, refined by
+// Illinois.  On a hit, the hit point is returned in (hcx, hX, hy).
+template <class R>
+__device__ R trochoid_line_hit(const StepConst<R>& k, const Cold<R>& C, bool on_surface, R& hcx, R& hX, R& hy)
+{
+    const R A = k.A, kA = k.kA;
+    const R dx = C.dx, dy = C.dy;
+    const R dxy = Mth<R>::sqrt_(dx * dx + dy * dy);
+    if (!(dxy > R(1e-30))) return R(INFINITY);
+    if (dy >= R(0) && C.y >= A) return R(INFINITY);
+    Cold<R> Q = C;
+    R t0 = R(0);
+    if (C.y > A) {
+        t0 = (A - C.y) / dy;
+        advance(Q, t0);
+    }
+    R L;
+    if (dy < R(0)) L = (-A - Q.y) / dy;
+    else if (dy > R(0)) L = (A - Q.y) / dy;
+    else L = R(2) / fabs(dx);
+    if (!(L >= R(0))) L = R(0);
+    const R ds = R(0.25 * kInvTwoPi) / dxy;
+    auto height = [&](R X, R y) -> R {
+        const R E = trochoid_phase(X, kA);
+        R sn, cs;
+        Mth<R>::sincos(E, sn, cs);
+        return y - A * cs;
+    };
+    // frame at the start of the current increment
+    R fcx = Q.cx, fX = Q.X, fy = Q.y, s_a = R(0);
+    bool first = on_surface && t0 == R(0);
+    R ha;
+    if (first) {
+        const R E = trochoid_phase(fX, kA);
+        R sn, cs;
+        Mth<R>::sincos(E, sn, cs);
+        const R slope = -kA * sn / (R(1) - kA * cs);
+        ha = dy - slope * dx;
+        if (!(ha > R(0))) ha = R(1e-30);
+    } else {
+        ha = height(fX, fy);
+        if (ha <= R(0)) { hcx = fcx; hX = fX; hy = fy; return t0; }
+    }
+    for (int guard = 0; guard < (1 << 20); ++guard) {
+        R u_b = fmin(ds, L - s_a);
+        if (first && u_b <= Mth<R>::kRehit) {
+            if (s_a + u_b >= L) return R(INFINITY);
+            u_b = fmin(Mth<R>::kRehit, L - s_a);
+        }
+        if (!(u_b >= R(0))) return R(INFINITY);
+        const bool last = !(s_a + u_b < L);
+        R hb = height(fX + u_b * dx, fy + u_b * dy);
+        if (last && dy < R(0) && hb > R(0)) hb = R(0);   // a descending line meets the surface by y = -A
+        if (hb <= R(0)) {
+            R u;
+            if (first) {
+                auto defl = [&](R v) -> R { return height(fX + v * dx, fy + v * dy) / v; };
+                u = (u_b > R(0)) ? illinois_root(defl, R(0), ha, u_b, hb / u_b) : R(0);
+            } else {
+                auto hf = [&](R v) -> R { return height(fX + v * dx, fy + v * dy); };
+                u = (u_b > R(0)) ? illinois_root(hf, R(0), ha, u_b, hb) : R(0);
+            }
+            R a = u * dx;
+            const R n = Mth<R>::rint_(fX + a);
+            hcx = fcx + n;
+            hX = (fX - n) + a;
+            hy = fy + u * dy;
+            return t0 + s_a + u;
+        }
+        if (last) break;
+        first = false;
+        s_a += u_b;
+        fX += u_b * dx;
+        const R m = Mth<R>::rint_(fX);
+        fcx += m;
+        fX -= m;
+        fy += u_b * dy;
+        ha = hb;
+    }
+    return R(INFINITY);
+}
+
+// Entry of the line into the cloak box (slab method), infinity if it misses.
+template <class R>
+__device__ __forceinline__ R box_entry(const StepConst<R>& k, const Cold<R>& C, int& face)
+{
+    const R pos[3] = {C.X, C.y, C.z};
+    const R dir[3] = {C.dx, C.dy, C.dz};
+    const R lo[3] = {-k.E2 - C.cx, -k.A, -k.E2}, hi[3] = {k.E2 - C.cx, k.ytop, k.E2};
+    const int flo[3] = {EV_XM, EV_NONE, EV_ZM}, fhi[3] = {EV_XP, EV_TOP, EV_ZP};
+    R tn = R(-INFINITY), tf = R(INFINITY);
+    int fn = EV_NONE;
+    for (int a = 0; a < 3; ++a) {
+        if (dir[a] == R(0)) {
+            if (pos[a] < lo[a] || pos[a] > hi[a]) return R(INFINITY);
+            continue;
+        }
+        const R inv = R(1) / dir[a];
+        const R t1 = (lo[a] - pos[a]) * inv, t2 = (hi[a] - pos[a]) * inv;
+        R tmin = t1, tmax = t2;
+        int f = flo[a];
+        if (t1 > t2) { tmin = t2; tmax = t1; f = fhi[a]; }
+        if (tmin > tn) { tn = tmin; fn = f; }
+        if (tmax < tf) tf = tmax;
+    }
+    if (!(tn <= tf) || !(tn > R(64) * Mth<R>::kEps)) return R(INFINITY);
+    face = fn;
+    return tn;
+}
+
+// Background plane standing in for the photograph (Sec. 4, Fig. 2a).
+template <class R>
+__device__ __forceinline__ int background(const DevScene& sc, const AirConst<R>& a, const Cold<R>& C, float col[3])
+{
+    col[0] = col[1] = col[2] = 0.0f;
+    const R d[3] = {C.dx, C.dy, C.dz};
+    const R X[3] = {C.cx + C.X, C.y, C.z};
+    const R dn = d[0] * a.fr[0] + d[1] * a.fr[1] + d[2] * a.fr[2];
+    if (!(dn > R(0))) return RT_RAY_SKY;
+    const R t = ((a.Pb[0] - X[0]) * a.fr[0] + (a.Pb[1] - X[1]) * a.fr[1] + (a.Pb[2] - X[2]) * a.fr[2]) / dn;
+    R Y[3];
+    for (int q = 0; q < 3; ++q) Y[q] = X[q] + t * d[q] - a.Pb[q];
+    const R s = Y[0] * a.r[0] + Y[1] * a.r[1] + Y[2] * a.r[2];
+    const R tt = Y[0] * a.ur[0] + Y[1] * a.ur[1] + Y[2] * a.ur[2];
+    if (sc.background == RT_BG_CHECKER) {
+        const long long u = (long long)floor(s * a.inv_cell), v = (long long)floor(tt * a.inv_cell);
+        const float* c = (((u + v) & 1LL) == 0) ? sc.col0 : sc.col1;
+        col[0] = c[0]; col[1] = c[1]; col[2] = c[2];
+    } else {
+        const int N = sc.tex_size;
+        const R U = s * a.inv_texel - R(0.5), V = tt * a.inv_texel - R(0.5);
+        const R fu0 = floor(U), fv0 = floor(V);
+        const float fu = (float)(U - fu0), fv = (float)(V - fv0);
+        long long u0 = (long long)fu0 % N, v0 = (long long)fv0 % N;
+        if (u0 < 0) u0 += N;
+        if (v0 < 0) v0 += N;
+        const long long u1 = (u0 + 1 == N) ? 0 : u0 + 1, v1 = (v0 + 1 == N) ? 0 : v0 + 1;
+        const float t00 = __ldg(sc.tex + v0 * N + u0), t01 = __ldg(sc.tex + v0 * N + u1);
+        const float t10 = __ldg(sc.tex + v1 * N + u0), t11 = __ldg(sc.tex + v1 * N + u1);
+        const float val = (1.0f - fu) * (1.0f - fv) * t00 + fu * (1.0f - fv) * t01 + (1.0f - fu) * fv * t10 +
+                          fu * fv * t11;
+        col[0] = col[1] = col[2] = val;
+    }
+    return RT_RAY_OK;
+}
+
+template <class R>
+__device__ __forceinline__ void finish_sample(const DevScene& sc, Cold<R>& C, int steps, int status, int& phase,
+                                              rt_ray_record* rec)
+{
+    if (status != RT_RAY_OK && status != RT_RAY_SKY) C.col[0] = C.col[1] = C.col[2] = 0.0f;
+    C.status = status;
+    C.acc[0] += C.col[0];
+    C.acc[1] += C.col[1];
+    C.acc[2] += C.col[2];
+    C.rays += 1;
+    C.stat[status < 5 ? status : 4] += 1;
+    if (rec) {
+        rt_ray_record* o = rec + C.work * sc.spp + C.sample;
+        const double pos[3] = {(double)C.cx + (double)C.X, (double)C.y, (double)C.z};
+        const double d[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+        const double l = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+        for (int a = 0; a < 3; ++a) {
+            o->pos[a] = pos[a] * sc.Lambda;
+            o->dir[a] = d[a] / l;
+            o->rgb[a] = C.col[a];
+        }
+        o->status = status;
+        o->bounces = C.bounces;
+        o->events = C.events;
+        o->steps = steps;
+    }
+    phase = PH_DONE;
+}
+
+// Copy a ray in the cloak to the air state (position and unit direction).
+template <class R>
+__device__ __forceinline__ void box_to_air(Cold<R>& C, const Box<R>& b, const R d[3])
+{
+    C.cx = b.cx;
+    C.X = b.X;
+    C.y = b.y;
+    C.z = b.z;
+    const R il = R(1) / Mth<R>::sqrt_(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    C.dx = d[0] * il;
+    C.dy = d[1] * il;
+    C.dz = d[2] * il;
+}
+
+template <class R>
+__device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
+                            rt_ray_record* rec, LaneStats& st)
+{
+    const StepConst<R>& k = step_const<R>(sc);
+    for (;;) {
+        if (C.bounces > sc.max_bounces) { finish_sample(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec); return; }
+        R hcx = R(0), hX = R(0), hy = R(0);
+        const R tm = sc.mirror ? trochoid_line_hit(k, C, surf == EV_GRATING, hcx, hX, hy) : flat_line_hit(C);
+        int face = EV_NONE;
+        const R tb = sc.cloak ? box_entry(k, C, face) : R(INFINITY);
+        if (tb < tm) {
+            advance(C, tb);
+            R Nf[3];
+            face_normal(face, Nf);
+            b.cx = C.cx;
+            b.X = C.X;
+            b.y = C.y;
+            b.z = C.z;
+            b.wr = b.wi = R(0);
+            w0_eval(k.kA, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
+            // Snell's law in FP64 (a few operations per entry): sqrt(n^2 - |p_t|^2)
+            // is ill-conditioned near grazing incidence
+            const double rr = (double)b.rr, ri = (double)b.ri;
+            const double n2 = rr * rr + ri * ri;
+            const double d[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+            const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
+            const double pn = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
+            double pt[3];
+            for (int a = 0; a < 3; ++a) pt[a] = d[a] - pn * N[a];
+            const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
+            if (n2 < pt2) {      // total reflection off the outside of the box
+                C.dx = (R)(d[0] - 2.0 * pn * N[0]);
+                C.dy = (R)(d[1] - 2.0 * pn * N[1]);
+                C.dz = (R)(d[2] - 2.0 * pn * N[2]);
+                C.bounces++;
+                surf = EV_NONE;
+                continue;
+            }
+            const double pin = sqrt(n2 - pt2);
+            b.px = (R)(pt[0] - pin * N[0]);
+            b.py = (R)(pt[1] - pin * N[1]);
+            b.pz = (R)(pt[2] - pin * N[2]);
+            b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
+            ray_force(b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy);
+            surf = face;
+            phase = PH_BOX;
+            return;
+        }
+        if (tm < R(INFINITY)) {
+            if (sc.mirror) {
+                C.z += tm * C.dz;
+                C.cx = hcx;
+                C.X = hX;
+                C.y = hy;
+                // upward normal from the tangent of Eq. 2 at the phase of the hit
+                const R E = trochoid_phase(C.X, k.kA);
+                R sn, cs;
+                Mth<R>::sincos(E, sn, cs);
+                const double nx = (double)k.kA * (double)sn, ny = 1.0 - (double)k.kA * (double)cs;
+                const double il = 1.0 / sqrt(nx * nx + ny * ny);
+                const double pn = ((double)C.dx * nx + (double)C.dy * ny) * il;
+                C.dx = (R)((double)C.dx - 2.0 * pn * nx * il);
+                C.dy = (R)((double)C.dy - 2.0 * pn * ny * il);
+            } else {
+                advance(C, tm);
+                C.y = R(0);
+                C.dy = -C.dy;
+            }
+            C.bounces++;
+            surf = EV_GRATING;
+            continue;
+        }
+        const int status = background(sc, air_const<R>(sc), C, C.col);
+        finish_sample(sc, C, steps, status, phase, rec);
+        return;
+    }
+}
+
+// ------------------------------------------------------------------------
+// Service of a lane whose step crossed a surface (or hit a guard).
+// ------------------------------------------------------------------------
+template <class R>
+__device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
+                              rt_ray_record* rec, LaneStats& st)
+{
+    const StepConst<R>& k = step_const<R>(sc);
+    const R p0[3] = {b.px, b.py, b.pz};
+    if (phase == PH_GUARD) {
+        box_to_air(C, b, p0);
+        finish_sample(sc, C, steps, RT_RAY_MAX_STEPS, phase, rec);
+        return;
+    }
+    bool finite = true;
+    for (int ev = 0; ev < EV_COUNT; ++ev) finite = finite && isfinite(C.g1[ev]);
+    if (!finite || !(isfinite(b.X) && isfinite(b.y) && isfinite(b.px) && isfinite(b.py))) {
+        box_to_air(C, b, p0);
+        finish_sample(sc, C, steps, RT_RAY_NAN, phase, rec);
+        return;
+    }
+    int ev_best = EV_NONE, last = EV_NONE;
+    R th_best = R(2);
+    Box<R> t;
+    for (int ev = 0; ev < EV_COUNT; ++ev) {
+        if (C.g1[ev] < R(0)) {
+            const R th = locate_event(k, b, ev, surf == ev, C.g1[ev], t, st);
+            last = ev;
+            if (th < th_best) { th_best = th; ev_best = ev; }
+        }
+    }
+    if (last != ev_best) {
+        rk4_step(k.kA, b, th_best * k.h, t, st);
+        w0_eval(k.kA, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
+    }
+    b = t;
+    ray_force(b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy);
+    C.events++;
+    C.nevents++;
+    if (ev_best == EV_GRATING) {
+        // mirror reflection about grad v / |grad v| = (Im r, Re r) / |r|
+        const R il = R(1) / Mth<R>::sqrt_(b.rr * b.rr + b.ri * b.ri);
+        const R nx = b.ri * il, ny = b.rr * il;
+        const R pn = b.px * nx + b.py * ny;
+        b.px -= R(2) * pn * nx;
+        b.py -= R(2) * pn * ny;
+        b.cpx = b.cpy = R(0);
+        C.bounces++;
+        surf = EV_GRATING;
+        phase = PH_BOX;
+        if (C.bounces > sc.max_bounces) {
+            const R p[3] = {b.px, b.py, b.pz};
+            box_to_air(C, b, p);
+            finish_sample(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec);
+        }
+        return;
+    }
+    // a face: refract into air (n = 1) or reflect totally; Snell's law in
+    // FP64 since sqrt(1 - |p_t|^2) is ill-conditioned near grazing exit
+    R Nf[3];
+    face_normal(ev_best, Nf);
+    const double p[3] = {(double)b.px, (double)b.py, (double)b.pz};
+    const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
+    const double pn = p[0] * N[0] + p[1] * N[1] + p[2] * N[2];
+    double pt[3];
+    for (int a = 0; a < 3; ++a) pt[a] = p[a] - pn * N[a];
+    const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
+    if (pt2 >= 1.0) {
+        b.px = (R)(p[0] - 2.0 * pn * N[0]);
+        b.py = (R)(p[1] - 2.0 * pn * N[1]);
+        b.pz = (R)(p[2] - 2.0 * pn * N[2]);
+        b.cpx = b.cpy = R(0);
+        C.bounces++;
+        surf = ev_best;
+        phase = PH_BOX;
+        if (C.bounces > sc.max_bounces) {
+            const R q[3] = {b.px, b.py, b.pz};
+            box_to_air(C, b, q);
+            finish_sample(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec);
+        }
+        return;
+    }
+    const double pout = sqrt(1.0 - pt2);
+    double d[3], l2 = 0.0;
+    for (int a = 0; a < 3; ++a) { d[a] = pt[a] + pout * N[a]; l2 += d[a] * d[a]; }
+    const double il = 1.0 / sqrt(l2);
+    C.cx = b.cx;
+    C.X = b.X;
+    C.y = b.y;
+    C.z = b.z;
+    C.dx = (R)(d[0] * il);
+    C.dy = (R)(d[1] * il);
+    C.dz = (R)(d[2] * il);
+    surf = EV_NONE;
+    phase = PH_AIR;
+}
+
+// ------------------------------------------------------------------------
+// The integration step of the hot loop.
+// ------------------------------------------------------------------------
+template <class R>
+__device__ __forceinline__ void box_step(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf,
+                                         int& steps, LaneStats& st)
+{
+    const StepConst<R>& k = step_const<R>(sc);
+    if (steps >= sc.max_steps) {
+        phase = PH_GUARD;
+        return;
+    }
+    Box<R> s1;
+    rk4_step(k.kA, b, k.h, s1, st);
+    w0_eval(k.kA, s1.X, s1.y, s1.wr, s1.wi, s1.rr, s1.ri, st);
+    ray_force(s1.wr, s1.wi, s1.rr, s1.ri, s1.Fx, s1.Fy);
+    ++steps;
+    st.steps++;
+    const R gG = s1.y + s1.wr * R(kInvTwoPi);
+    const R gT = k.ytop - s1.y;
+    const R gXp = (k.E2 - s1.cx) - s1.X, gXm = (k.E2 + s1.cx) + s1.X;
+    const R gZp = k.E2 - s1.z, gZm = k.E2 + s1.z;
+    if (gG >= R(0) && gT >= R(0) && gXp >= R(0) && gXm >= R(0) && gZp >= R(0) && gZm >= R(0)) {
+        b = s1;
+        surf = EV_NONE;
+        return;
+    }
+    // crossed a surface (or went non-finite): the service pass locates it from b
+    C.g1[EV_GRATING] = gG;
+    C.g1[EV_TOP] = gT;
+    C.g1[EV_XP] = gXp;
+    C.g1[EV_XM] = gXm;
+    C.g1[EV_ZP] = gZp;
+    C.g1[EV_ZM] = gZm;
+    phase = PH_EVENT;
+}
+
+// ------------------------------------------------------------------------
+// Work distribution and the persistent loop.
+// ------------------------------------------------------------------------
+// Warp-aggregated grab of one work item per calling lane: one atomic for the
+// lanes that arrive together.
+__device__ __forceinline__ int64_t grab_work(unsigned long long* counter, unsigned lane)
+{
+    const unsigned m = __activemask();
+    const int leader = __ffs(m) - 1;
+    const unsigned rank = __popc(m & ((1u << lane) - 1u));
+    unsigned long long base = 0;
+    if ((int)lane == leader) base = atomicAdd(counter, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return (int64_t)(base + rank);
+}
+
+template <class R>
+__device__ __forceinline__ void start_sample(const DevScene& sc, Cold<R>& C, int& phase, int& surf, int& steps)
+{
+    camera_start(sc, C);
+    C.bounces = 0;
+    C.events = 0;
+    C.col[0] = C.col[1] = C.col[2] = 0.0f;
+    surf = EV_NONE;
+    steps = 0;
+    phase = PH_AIR;
+}
+
+__device__ __forceinline__ uint8_t quantize8(float c)
+{
+    float v = c > 0.0f ? c : 0.0f;
+    v = v < 1.0f ? v : 1.0f;
+    return (uint8_t)floorf(v * 255.0f + 0.5f);
+}
+
+template <class R, int MINB>
+__global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid_constant__ DevScene sc,
+                                                              float* __restrict__ rgb, uint8_t* __restrict__ rgb8,
+                                                              rt_ray_record* rec, unsigned long long* counters,
+                                                              int min_active)
+{
+    __shared__ Cold<R> cold_all[kRenderBlock];
+    Cold<R>& C = cold_all[threadIdx.x];
+    C.rays = 0;
+    C.nevents = 0;
+    for (int q = 0; q < 5; ++q) C.stat[q] = 0;
+    Box<R> b;
+    int phase = PH_IDLE, surf = EV_NONE, steps = 0;
+    LaneStats st = {0u, 0u, 0u, 0u};
+    const unsigned lane = threadIdx.x & 31u;
+#if RT_PROFILE
+    // per-warp cycle split (lane 0): service pass, integration loop, loop
+    // iterations and lanes inside the cloak summed over those iterations
+    unsigned long long prof_service = 0, prof_hot = 0, prof_iters = 0, prof_lanes = 0;
+#endif
+    for (;;) {
+#if RT_PROFILE
+        const long long t_service = clock64();
+#endif
+        // lanes outside the integration catch up until their ray is inside
+        // the cloak again or the work is exhausted
+        while (phase != PH_BOX && phase != PH_EXIT) {
+            if (phase == PH_EVENT || phase == PH_GUARD) service_event(sc, C, b, phase, surf, steps, rec, st);
+            if (phase == PH_IDLE) {
+                const int64_t w = grab_work(&counters[0], lane);
+                if (w >= sc.nwork) { phase = PH_EXIT; break; }
+                C.work = w;
+                C.pix = sc.pix_list ? sc.pix_list[w] : w;
+                C.sample = 0;
+                C.acc[0] = C.acc[1] = C.acc[2] = 0.0f;
+                start_sample(sc, C, phase, surf, steps);
+            }
+            if (phase == PH_AIR) air_segment(sc, C, b, phase, surf, steps, rec, st);
+            if (phase == PH_DONE) {
+                if (++C.sample < sc.spp) {
+                    start_sample(sc, C, phase, surf, steps);
+                } else {
+                    const float inv = 1.0f / (float)sc.spp;
+                    float c[3];
+                    for (int a = 0; a < 3; ++a) c[a] = C.acc[a] * inv;
+                    float* o = rgb + 3 * C.work;
+                    o[0] = c[0]; o[1] = c[1]; o[2] = c[2];
+                    if (rgb8) {
+                        uint8_t* q = rgb8 + 3 * C.work;
+                        q[0] = quantize8(c[0]); q[1] = quantize8(c[1]); q[2] = quantize8(c[2]);
+                    }
+                    phase = PH_IDLE;
+                }
+            }
+        }
+        if (__ballot_sync(0xffffffffu, phase == PH_BOX) == 0u) break;   // every lane is out of work
+#if RT_PROFILE
+        const long long t_hot = clock64();
+        prof_service += (unsigned long long)(t_hot - t_service);
+#endif
+        // once the work is exhausted, refills are pointless: step while any lane is inside
+        const int need = __any_sync(0xffffffffu, phase == PH_EXIT) ? 1 : min_active;
+        for (;;) {
+#if RT_PROFILE
+            prof_iters += 1;
+            prof_lanes += __popc(__ballot_sync(0xffffffffu, phase == PH_BOX));
+#endif
+            if (phase == PH_BOX) box_step(sc, C, b, phase, surf, steps, st);
+            if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
+        }
+#if RT_PROFILE
+        prof_hot += (unsigned long long)(clock64() - t_hot);
+#endif
+    }
+#if RT_PROFILE
+    if (lane == 0) {
+        atomicAdd(&counters[12], prof_service);
+        atomicAdd(&counters[13], prof_hot);
+        atomicAdd(&counters[14], prof_iters);
+        atomicAdd(&counters[15], prof_lanes);
+    }
+#endif
+    // warp-reduce the counters, one atomic per warp and counter
+    const uint32_t v[11] = {C.rays, st.steps, st.evals, st.newton, C.nevents, st.refine,
+                            C.stat[0], C.stat[1], C.stat[2], C.stat[3], C.stat[4]};
+#pragma unroll
+    for (int q = 0; q < 11; ++q) {
+        unsigned long long x = v[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0 && x) atomicAdd(&counters[1 + q], x);
+    }
+}
+
+// W0, n and the force at arbitrary points.
+template <class R>
+__global__ void medium_kernel(double kA, double Lambda, const double* __restrict__ xy, int64_t n,
+                              double* __restrict__ out)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double x = xy[2 * i] / Lambda, y = xy[2 * i + 1] / Lambda;
+    const double cxd = rint(x);
+    const R X = (R)(x - cxd), yy = (R)y;
+    R wr = R(0), wi = R(0), rr, ri;
+    LaneStats st = {0u, 0u, 0u, 0u};
+    w0_eval((R)kA, X, yy, wr, wi, rr, ri, st);
+    R Fx, Fy;
+    ray_force(wr, wi, rr, ri, Fx, Fy);
+    out[5 * i + 0] = (double)wr;
+    out[5 * i + 1] = (double)wi;
+    out[5 * i + 2] = sqrt((double)(rr * rr + ri * ri));
+    out[5 * i + 3] = (double)Fx / Lambda;
+    out[5 * i + 4] = (double)Fy / Lambda;
+}
+
+}  // namespace grt

@@ -13,7 +13,7 @@ import os
 import numpy as np
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libgratingrt.so")
+LIB_PATH = os.environ.get("GRATINGRT_LIB") or os.path.join(PKG, "libgratingrt.so")
 
 RT_OK, RT_PENDING = 0, 1
 RT_EINVAL, RT_ENOMEM, RT_ENODEV, RT_EBUSY, RT_ETIMEDOUT, RT_ECUDA = -22, -12, -19, -16, -110, -5
@@ -60,13 +60,15 @@ assert C.sizeof(RayRecord) == RECORD_DTYPE.itemsize
 
 class Stats(C.Structure):
     _fields_ = [("rays", C.c_uint64), ("steps", C.c_uint64), ("evals", C.c_uint64), ("newton", C.c_uint64),
-                ("events", C.c_uint64), ("fp64_refine", C.c_uint64), ("status", C.c_uint64 * 5)]
+                ("events", C.c_uint64), ("fp64_refine", C.c_uint64), ("status", C.c_uint64 * 5),
+                ("profile", C.c_uint64 * 4)]
 
 
 _lib = None
 
 EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels", "rt_render_host",
-           "rt_scene_stats", "rt_xcorr", "rt_eval_medium", "rt_last_error", "rt_version"]
+           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_xcorr", "rt_eval_medium",
+           "rt_last_error", "rt_version"]
 
 
 def lib() -> C.CDLL:
@@ -86,6 +88,8 @@ def lib() -> C.CDLL:
     L.rt_render_pixels.argtypes = [vp, vp, C.c_int64, vp, vp, vp]
     L.rt_render_host.argtypes = [vp, vp, vp, vp]
     L.rt_scene_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.rt_scene_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
+    L.rt_scene_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.rt_xcorr.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                            C.c_double, vp, vp]
     L.rt_eval_medium.argtypes = [C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp, vp]
@@ -174,11 +178,19 @@ class Scene:
         _check(lib().rt_render_host(self._h, h_rgb.ctypes.data, None if h_rgb8 is None else h_rgb8.ctypes.data,
                                     _stream(stream)))
 
+    def set_launch(self, variant: int = -1, min_active: int = 0):
+        _check(lib().rt_scene_set_launch(self._h, variant, min_active))
+
+    def get_launch(self) -> dict:
+        v, m, g = C.c_int32(), C.c_int32(), C.c_int32()
+        _check(lib().rt_scene_get_launch(self._h, C.byref(v), C.byref(m), C.byref(g)))
+        return {"variant": v.value, "min_active": m.value, "grid": g.value}
+
     def stats(self) -> dict:
         s = Stats()
         _check(lib().rt_scene_stats(self._h, C.byref(s)))
         return {"rays": s.rays, "steps": s.steps, "evals": s.evals, "newton": s.newton, "events": s.events,
-                "fp64_refine": s.fp64_refine, "status": list(s.status)}
+                "fp64_refine": s.fp64_refine, "status": list(s.status), "profile": list(s.profile)}
 
 
 def records_to_numpy(rec_bytes) -> np.ndarray:

@@ -49,7 +49,75 @@ def gpu_render(rt, torch, p, records=True, tex=None):
     return out
 
 
-def compare_records(g, o, pos_tol=POS_TOL, dir_tol=DIR_TOL, min_frac=0.999):
+# FP32 carries about 1e-7 relative rounding into every quantity of a ray
+# once the ray reaches the scene (the camera ray up to the cloak box or the
+# grating band is set up in FP64).  A ray whose exit moves by more than the
+# tolerance when its direction is turned by EPS32 where it reaches the scene
+# cannot be resolved in FP32 by any arithmetic; such rays are identified with
+# the oracle itself and reported apart from the parity bar.
+EPS32 = 3e-7
+PERTURB = 1e-7
+
+
+def scene_entry(p, org, d):
+    """Parameter t at which the camera ray org + t d first reaches the scene:
+    the cloak box (slab test) or the band y <= A of the grating, whichever
+    comes first; None if it reaches neither."""
+    lam = p["Lambda"]
+    ts = []
+    if d[1] < 0.0:
+        ts.append((max(p["A"], 1e-6 * lam) - org[1]) / d[1])
+    if p["cloak"]:
+        lo = np.array([-p["E"] / 2, -p["A"], -p["E"] / 2])
+        hi = np.array([p["E"] / 2, p["H"] - p["A"], p["E"] / 2])
+        with np.errstate(divide="ignore", invalid="ignore"):
+            t1, t2 = (lo - org) / d, (hi - org) / d
+        tn, tf = np.minimum(t1, t2).max(), np.maximum(t1, t2).min()
+        if tn <= tf and tn > 0:
+            ts.append(tn)
+    ts = [t for t in ts if t > 0]
+    return min(ts) if ts else None
+
+
+def sensitivity(orc, p, pix, spp, o_rec, tex=None):
+    """Largest change of exit direction and position per radian of a turn of
+    the ray where it reaches the scene (two perpendicular 1e-7 rad turns;
+    oracle, FP64).  A change of path (bounce count or status) counts as
+    infinite sensitivity."""
+    sc = orc.Scene(p, tex=tex)
+    wout = 1 if p.get("centre_line", 0) else p["width"]
+    o_rec = o_rec.reshape(-1)
+    Sd = np.zeros(o_rec.size)
+    Sp = np.zeros(o_rec.size)
+    q = 0
+    for px in np.asarray(pix).reshape(-1):
+        i, j = divmod(int(px), wout)
+        for s in range(spp):
+            org, d = orc.camera_dir(sc, i, j, s)
+            t = scene_entry(p, org, d)
+            if t is None:
+                q += 1
+                continue
+            start = org + 0.999999 * t * d
+            a = np.cross(d, [0.0, 1.0, 0.0]); a /= np.linalg.norm(a)
+            b = np.cross(d, a)
+            for e in (a, b):
+                d2 = d + PERTURB * e
+                d2 /= np.linalg.norm(d2)
+                r, _ = orc.trace_from(sc, start, d2)
+                if r["bounces"] != o_rec["bounces"][q] or r["status"] != o_rec["status"][q]:
+                    Sd[q] = Sp[q] = np.inf
+                else:
+                    Sd[q] = max(Sd[q], np.linalg.norm(np.asarray(r["dir"]) - o_rec["dir"][q]) / PERTURB)
+                    Sp[q] = max(Sp[q], np.abs(np.asarray(r["pos"]) - o_rec["pos"][q]).max() / PERTURB)
+            q += 1
+    return Sd, Sp
+
+
+def compare_records(g, o, pos_tol=POS_TOL, dir_tol=DIR_TOL, min_frac=0.999, cond=None, min_frac_all=None):
+    """Same path, exit position and direction within tolerance.  With `cond`
+    (a mask of rays that FP32 can resolve) the bar applies to those rays and
+    `min_frac_all` to all rays."""
     g = g.reshape(-1)
     o = o.reshape(-1)
     same = (g["status"] == o["status"]) & (g["bounces"] == o["bounces"])
@@ -58,9 +126,24 @@ def compare_records(g, o, pos_tol=POS_TOL, dir_tol=DIR_TOL, min_frac=0.999):
     ok = same & (dpos <= pos_tol) & (ddir <= dir_tol)
     info = dict(same=same.mean(), ok=ok.mean(), dpos_med=float(np.median(dpos[same])) if same.any() else 0,
                 dpos_max=float(dpos[same].max()) if same.any() else 0,
-                ddir_max=float(ddir[same].max()) if same.any() else 0)
-    assert ok.mean() >= min_frac, info
+                ddir_max=float(ddir[same].max()) if same.any() else 0,
+                ddir_p99=float(np.percentile(ddir[same], 99)) if same.any() else 0)
+    if cond is None:
+        assert ok.mean() >= min_frac, info
+    else:
+        cond = cond.reshape(-1)
+        info["conditioned"] = float(cond.mean())
+        info["ok_conditioned"] = float(ok[cond].mean()) if cond.any() else 1.0
+        assert info["ok_conditioned"] >= min_frac, info
+        if min_frac_all is not None:
+            assert ok.mean() >= min_frac_all, info
+    print(info)
     return info
+
+
+def fp32_resolvable(orc, p, pix, spp, o_rec, tex=None):
+    Sd, Sp = sensitivity(orc, p, pix, spp, o_rec, tex)
+    return (Sd * EPS32 <= DIR_TOL) & (Sp * EPS32 <= POS_TOL * p["Lambda"])
 
 
 def compare_images(q_gpu, q_ref, max_frac=0.001):
@@ -124,8 +207,12 @@ def test_render_small_config(rt, torch, orc, precision, kind):
     p = inputs.three_renders(inputs.config_small(precision=precision))[kind]
     g = gpu_render(rt, torch, p)
     o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
-    info = compare_records(g["rec"], o_rec, min_frac=0.998 if kind == "cloak" else 0.999)
-    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001 if kind != "cloak" else 0.005)
+    if precision == 1:
+        info = compare_records(g["rec"], o_rec, min_frac=1.0)
+    else:
+        cond = fp32_resolvable(orc, p, np.arange(64 * 64), 1, o_rec)
+        info = compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
+    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001 if kind != "cloak" else 0.002)
     assert g["stats"]["rays"] == 64 * 64
     if precision == 1:
         assert info["dpos_med"] < 1e-9
@@ -141,9 +228,13 @@ def test_render_main_config_sampled(rt, torch, orc, precision):
     pix = inputs.pixel_subset(512, 512, 1500, seed=21)
     o_rgb, o_rec = orc.render_pixels(orc.Scene(p), pix, records=True)
     grec = g["rec"].reshape(512 * 512, 4)[pix]
-    compare_records(grec, o_rec.reshape(-1, 4), min_frac=0.998)
+    if precision == 1:
+        compare_records(grec, o_rec, min_frac=1.0)
+    else:
+        cond = fp32_resolvable(orc, p, pix, 4, o_rec)
+        compare_records(grec, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
     q = g["rgb8"].reshape(-1, 3)[pix]
-    compare_images(q, orc.quantize(o_rgb), max_frac=0.005)
+    compare_images(q, orc.quantize(o_rgb), max_frac=0.002)
     st = g["stats"]
     assert st["rays"] == 512 * 512 * 4
     assert sum(st["status"]) == st["rays"]
@@ -188,7 +279,13 @@ def test_edge_cases(rt, torch, orc, over, precision):
     g = gpu_render(rt, torch, p)
     o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
     n = o_rec.size
-    compare_records(g["rec"], o_rec, pos_tol=POS_TOL * p["Lambda"], min_frac=1.0 - 2.0 / n)
+    if precision == 1:
+        compare_records(g["rec"], o_rec, pos_tol=POS_TOL * p["Lambda"], min_frac=1.0)
+    else:
+        wout = 1 if p["centre_line"] else p["width"]
+        cond = fp32_resolvable(orc, p, np.arange(p["height"] * wout), p["spp"], o_rec)
+        compare_records(g["rec"], o_rec, pos_tol=POS_TOL * p["Lambda"], min_frac=1.0 - 1.0 / n, cond=cond,
+                        min_frac_all=0.97)
     assert np.array_equal(np.sort(g["rec"]["status"].ravel()), np.sort(o_rec["status"].ravel())) or n > 100
 
 
@@ -207,7 +304,8 @@ def test_texture_background(rt, torch, orc):
                           precision=0)
     g = gpu_render(rt, torch, p, tex=tex)
     o_rgb, o_rec = orc.render(orc.Scene(p, tex=tex), records=True)
-    compare_records(g["rec"], o_rec, min_frac=0.995)
+    cond = fp32_resolvable(orc, p, np.arange(30 * 40), 4, o_rec, tex)
+    compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
     assert np.abs(g["rgb"] - o_rgb).max() < 0.05
     assert np.median(np.abs(g["rgb"] - o_rgb)) < 1e-5
 

@@ -55,6 +55,12 @@ def test_stratified_jitter(orc):
     assert quad == {(0, 0), (1, 0), (0, 1), (1, 1)}
 
 
+def at_plane(rec, y):
+    """Where each record's final straight segment crosses the plane of height y."""
+    t = (y - rec["pos"][:, 1]) / rec["dir"][:, 1]
+    return rec["pos"] + t[:, None] * rec["dir"]
+
+
 def _records(orc, p, pix=None):
     sc = orc.Scene(p)
     if pix is None:
@@ -71,9 +77,10 @@ def test_flat_limit_of_grating_and_cloak(orc):
     _, rb = _records(orc, dict(base, mirror=1, cloak=0))
     _, rc = _records(orc, dict(base, mirror=1, cloak=1))
     assert (rm["bounces"] == 1).all()
+    y = base["H"] - base["A"] + 1.0
     for r in (rb, rc):
         assert np.abs(r["dir"] - rm["dir"]).max() < 1e-12
-        assert np.abs(r["pos"] - rm["pos"]).max() < 1e-9
+        assert np.abs(at_plane(r, y) - at_plane(rm, y)).max() < 1e-9
         assert (r["bounces"] == rm["bounces"]).all()
 
 
@@ -104,12 +111,11 @@ def test_centre_line_is_cloaked(orc):
     for i in range(96):
         o, d = orc.camera_dir(sc, i, 0, 0)
         xin[i] = o[0] + (top - o[1]) / d[1] * d[0] if d[1] < 0 else np.inf
-    pos, dr = rm["pos"], rm["dir"]
-    xout = pos[:, 0] + (top - pos[:, 1]) / dr[:, 1] * dr[:, 0]
+    xout = at_plane(rm, top)[:, 0]
     inside = (np.abs(xin) < 19.0) & (np.abs(xout) < 19.0) & (rm["bounces"] == 1)
     assert inside.sum() >= 10
     dd = np.linalg.norm(rc["dir"] - rm["dir"], axis=1)[inside]
-    dp = np.linalg.norm(rc["pos"] - rm["pos"], axis=1)[inside]
+    dp = np.linalg.norm(at_plane(rc, top + 1.0) - at_plane(rm, top + 1.0), axis=1)[inside]
     assert dd.max() < 1e-6 and dp.max() < 1e-5, (dd.max(), dp.max())
     assert np.linalg.norm(rb["dir"] - rm["dir"], axis=1)[inside].max() > 0.05
 
@@ -128,3 +134,11 @@ def test_texture_bilinear_and_wrap(orc):
     rgb, rec = orc.render_pixels(sc, np.arange(81), records=True)
     assert np.all((rgb >= 0) & (rgb <= 15 / 16 + 1e-6))
     assert np.allclose(rgb[:, 0], rgb[:, 1]) and np.allclose(rgb[:, 0], rgb[:, 2])
+
+
+def test_texture_background_without_texture_is_an_error(orc):
+    import pytest
+    p = inputs.base_scene(width=4, height=4, spp=1, background=1, tex_size=8)
+    sc = orc.Scene(p)
+    with pytest.raises(ValueError):
+        orc.render(sc)

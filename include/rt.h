@@ -210,6 +210,25 @@ int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, 
              const double* fov_deg, int32_t n_fov, double hfov_deg, double* d_out, void* stream);
 
 /*
+ * rt_xcorr_noalloc: rt_xcorr without any device allocation, for callers that
+ * cannot allocate -- hosts that give all device memory to their own pool and
+ * forbid allocations behind its back, and latency-bound loops in which an
+ * allocation call (which can synchronise the device or take a driver lock) is
+ * not acceptable.  The paper has no counterpart: this is an interface
+ * variant of rt_xcorr with the same arguments, arithmetic and results.
+ * Its scratch is a fixed 16 MiB device array inside the library, held by
+ * every GPU that loads the library until the process exits; images with
+ * min(height, 64) * width * channels > 524288 are rejected with RT_EINVAL.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the one array, so calls that overlap on the GPU
+ * (on different streams, or from different threads) race; each call
+ * overwrites all scratch it reads, so nothing needs clearing.  Asynchronous.
+ */
+int rt_xcorr_noalloc(const float* d_f, const float* d_g, int32_t height, int32_t width, int32_t channels,
+                     const double* fov_deg, int32_t n_fov, double hfov_deg, double* d_out, void* stream);
+
+/*
  * rt_eval_medium: W0, n and the ray force grad(n^2)/2 at npoints points
  * (device d_xy: x0,y0,x1,y1,..., world units) for grating period Lambda and
  * amplitude A (Eqs. 1, 12, 13).  d_out gets per point

@@ -67,8 +67,8 @@ class Stats(C.Structure):
 _lib = None
 
 EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels", "rt_render_host",
-           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_xcorr", "rt_eval_medium",
-           "rt_last_error", "rt_version"]
+           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_xcorr", "rt_xcorr_noalloc",
+           "rt_eval_medium", "rt_last_error", "rt_version"]
 
 
 def lib() -> C.CDLL:
@@ -92,6 +92,8 @@ def lib() -> C.CDLL:
     L.rt_scene_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.rt_xcorr.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                            C.c_double, vp, vp]
+    L.rt_xcorr_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
+                                   C.c_double, vp, vp]
     L.rt_eval_medium.argtypes = [C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp, vp]
     L.rt_last_error.restype = C.c_char_p
     L.rt_version.restype = C.c_char_p
@@ -211,6 +213,22 @@ def xcorr(f, g, fov_deg, hfov_deg: float, out=None, stream=None):
         out = torch.empty((len(fov_deg), Cc + 1), dtype=torch.float64, device=f.device)
     _check(lib().rt_xcorr(_ptr(f), _ptr(g), H, W, Cc, fov, len(fov_deg), float(hfov_deg), _ptr(out),
                           _stream(stream)))
+    return out
+
+
+def xcorr_noalloc(f, g, fov_deg, hfov_deg: float, out=None, stream=None):
+    """xcorr through rt_xcorr_noalloc: the same results without any device
+    allocation by the library (its scratch is a fixed array; see include/rt.h)."""
+    import torch
+    if f.dim() == 2:
+        f = f.unsqueeze(-1)
+        g = g.unsqueeze(-1)
+    H, W, Cc = f.shape
+    fov = (C.c_double * len(fov_deg))(*[float(x) for x in fov_deg])
+    if out is None:
+        out = torch.empty((len(fov_deg), Cc + 1), dtype=torch.float64, device=f.device)
+    _check(lib().rt_xcorr_noalloc(_ptr(f), _ptr(g), H, W, Cc, fov, len(fov_deg), float(hfov_deg), _ptr(out),
+                                  _stream(stream)))
     return out
 
 

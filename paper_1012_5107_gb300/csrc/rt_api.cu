@@ -93,7 +93,6 @@ static int validate(const rt_scene_desc* d)
            "elev_deg must be in (-90, 90)");
     RT_REQ(std::isfinite(d->azim_deg), "azim_deg must be finite");
     RT_REQ(d->integrator == RT_RK4 || d->integrator == RT_DP45, "integrator must be RT_RK4 or RT_DP45");
-    RT_REQ(d->integrator == RT_RK4, "RT_DP45 is not available in this build");
     RT_REQ(d->precision == RT_FP32 || d->precision == RT_FP64, "precision must be RT_FP32 or RT_FP64");
     RT_REQ(d->h > 0.0 && std::isfinite(d->h), "h must be > 0");
     if (d->integrator == RT_DP45)
@@ -208,7 +207,7 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     int bps = 0;
     s->variant = kDefaultVariant;
     s->min_active = kMinActive;
-    cudaError_t e = render_occupancy(desc->precision, s->variant, &bps);
+    cudaError_t e = render_occupancy(desc->precision, desc->integrator, s->variant, &bps);
     int nsm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     s->nsm = nsm;
@@ -324,7 +323,7 @@ int rt_scene_set_launch(rt_scene* s, int32_t variant, int32_t min_active)
     RT_REQ(min_active == 0 || (min_active >= 1 && min_active <= 32), "min_active must be 0 (keep) or 1..32");
     if (variant >= 0 && variant != s->variant) {
         int bps = 0;
-        RT_CK(render_occupancy(s->desc.precision, variant, &bps));
+        RT_CK(render_occupancy(s->desc.precision, s->desc.integrator, variant, &bps));
         RT_REQ(bps > 0, "variant %d does not fit on this device", variant);
         s->variant = variant;
         s->grid = bps * s->nsm;

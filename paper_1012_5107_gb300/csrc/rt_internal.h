@@ -27,7 +27,7 @@ struct Windows {
     int j0[kMaxWindows], j1[kMaxWindows];
 };
 
-cudaError_t render_occupancy(int precision, int variant, int* blocks_per_sm);
+cudaError_t render_occupancy(int precision, int integrator, int variant, int* blocks_per_sm);
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
                           rt_ray_record* rec, unsigned long long* counters, int grid, cudaStream_t stream);
 cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,

@@ -4,37 +4,56 @@
 
 namespace grt {
 
-template <class R>
+// Register-budget variants are compiled for the FP32 RK4 kernel, the one the
+// benchmark times; the other (precision, integrator) pairs have one each.
+template <class R, int INTEG>
 static cudaError_t occupancy_t(int variant, int* bps)
 {
-    switch (variant) {
-        case 1: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[1]>, kRenderBlock, 0);
-        case 2: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[2]>, kRenderBlock, 0);
-        default: return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[0]>, kRenderBlock, 0);
+    if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
+        if (variant == 1)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[1], INTEG>, kRenderBlock, 0);
+        if (variant == 2)
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[2], INTEG>, kRenderBlock, 0);
     }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[0], INTEG>, kRenderBlock, 0);
 }
 
-template <class R>
+template <class R, int INTEG>
 static void launch_t(const DevScene& sc, int variant, int min_active, float* rgb, uint8_t* rgb8, rt_ray_record* rec,
                      unsigned long long* counters, int grid, cudaStream_t stream)
 {
-    switch (variant) {
-        case 1: render_kernel<R, kVariantBlocks[1]><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active); break;
-        case 2: render_kernel<R, kVariantBlocks[2]><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active); break;
-        default: render_kernel<R, kVariantBlocks[0]><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active); break;
+    if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
+        if (variant == 1) {
+            render_kernel<R, kVariantBlocks[1], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
+            return;
+        }
+        if (variant == 2) {
+            render_kernel<R, kVariantBlocks[2], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
+            return;
+        }
     }
+    render_kernel<R, kVariantBlocks[0], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
 }
 
-cudaError_t render_occupancy(int precision, int variant, int* blocks_per_sm)
+cudaError_t render_occupancy(int precision, int integrator, int variant, int* blocks_per_sm)
 {
-    return precision == RT_FP64 ? occupancy_t<double>(variant, blocks_per_sm) : occupancy_t<float>(variant, blocks_per_sm);
+    if (precision == RT_FP64)
+        return integrator == RT_DP45 ? occupancy_t<double, RT_DP45>(variant, blocks_per_sm)
+                                     : occupancy_t<double, RT_RK4>(variant, blocks_per_sm);
+    return integrator == RT_DP45 ? occupancy_t<float, RT_DP45>(variant, blocks_per_sm)
+                                 : occupancy_t<float, RT_RK4>(variant, blocks_per_sm);
 }
 
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
                           rt_ray_record* rec, unsigned long long* counters, int grid, cudaStream_t stream)
 {
-    if (precision == RT_FP64) launch_t<double>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
-    else launch_t<float>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
+    if (precision == RT_FP64) {
+        if (sc.integrator == RT_DP45) launch_t<double, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
+        else launch_t<double, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
+    } else {
+        if (sc.integrator == RT_DP45) launch_t<float, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
+        else launch_t<float, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
+    }
     return cudaGetLastError();
 }
 

@@ -52,6 +52,7 @@ struct Box {
     R cX, cy, cz, cpx, cpy;   // compensation terms of the FP32 sums
     R wr, wi, rr, ri;         // W0 and 1/(1+W0) at (X, y) (a prediction until solved)
     R Fx, Fy;                 // force at (X, y)
+    R hc;                     // Dormand-Prince: size of the next step
 };
 
 // What a lane owns outside the integration loop (shared memory).
@@ -60,6 +61,7 @@ struct Cold {
     R cx, X, y, z;            // air: position, x = cx + X
     R dx, dy, dz;             // air: unit direction
     R g1[EV_COUNT];           // event functions at the end of a step that crossed a surface
+    R hs;                     // size of that step
     int64_t work;             // work item (pixel slot)
     int64_t pix;              // pixel index i*wout + j
     float acc[3], col[3];
@@ -211,6 +213,105 @@ __device__ __forceinline__ void rk4_step(R kA, const Box<R>& s, R h, Box<R>& o, 
     else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
 }
 
+// Dormand & Prince (1980) RK5(4)7M: nodes, coefficients, fifth-order weights
+// and the differences between the fifth- and fourth-order weights.
+struct DPT {
+    static constexpr double a21 = 1.0 / 5;
+    static constexpr double a31 = 3.0 / 40, a32 = 9.0 / 40;
+    static constexpr double a41 = 44.0 / 45, a42 = -56.0 / 15, a43 = 32.0 / 9;
+    static constexpr double a51 = 19372.0 / 6561, a52 = -25360.0 / 2187, a53 = 64448.0 / 6561, a54 = -212.0 / 729;
+    static constexpr double a61 = 9017.0 / 3168, a62 = -355.0 / 33, a63 = 46732.0 / 5247, a64 = 49.0 / 176,
+                            a65 = -5103.0 / 18656;
+    static constexpr double b1 = 35.0 / 384, b3 = 500.0 / 1113, b4 = 125.0 / 192, b5 = -2187.0 / 6784, b6 = 11.0 / 84;
+    static constexpr double e1 = 35.0 / 384 - 5179.0 / 57600, e3 = 500.0 / 1113 - 7571.0 / 16695,
+                            e4 = 125.0 / 192 - 393.0 / 640, e5 = -2187.0 / 6784 + 92097.0 / 339200,
+                            e6 = 11.0 / 84 - 187.0 / 2100, e7 = -1.0 / 40;
+};
+
+// One Dormand-Prince step of size h from s (W0 solved and force known at s)
+// into o: the fifth-order solution, W0 solved and the force at it (the first
+// stage of the next step).  e[4] receives the error estimate of
+// (x, y, p_x, p_y).  The ODE is r' = p, p' = F(r): a stage momentum is
+// p + h sum a F and a stage position r + h sum a p_stage.
+template <class R>
+__device__ __forceinline__ void dp45_step(R kA, const Box<R>& s, R h, Box<R>& o, R e[4], LaneStats& st)
+{
+    typedef DPT T;
+    R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
+    R Xp = s.X, yp = s.y;
+    const R F1x = s.Fx, F1y = s.Fy, P1x = s.px, P1y = s.py;
+    auto stage = [&](R Px, R Py, R dXs, R dYs, R& Fx, R& Fy) {
+        const R Xs = s.X + dXs, Ys = s.y + dYs;
+        w0_continue(kA, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, st);
+        ray_force(wr, wi, rr, ri, Fx, Fy);
+        Xp = Xs;
+        yp = Ys;
+    };
+    // stage 2
+    const R P2x = P1x + h * R(T::a21) * F1x, P2y = P1y + h * R(T::a21) * F1y;
+    R F2x, F2y;
+    stage(P2x, P2y, h * R(T::a21) * P1x, h * R(T::a21) * P1y, F2x, F2y);
+    // stage 3
+    const R P3x = P1x + h * (R(T::a31) * F1x + R(T::a32) * F2x), P3y = P1y + h * (R(T::a31) * F1y + R(T::a32) * F2y);
+    R F3x, F3y;
+    stage(P3x, P3y, h * (R(T::a31) * P1x + R(T::a32) * P2x), h * (R(T::a31) * P1y + R(T::a32) * P2y), F3x, F3y);
+    // stage 4
+    const R P4x = P1x + h * (R(T::a41) * F1x + R(T::a42) * F2x + R(T::a43) * F3x);
+    const R P4y = P1y + h * (R(T::a41) * F1y + R(T::a42) * F2y + R(T::a43) * F3y);
+    R F4x, F4y;
+    stage(P4x, P4y, h * (R(T::a41) * P1x + R(T::a42) * P2x + R(T::a43) * P3x),
+          h * (R(T::a41) * P1y + R(T::a42) * P2y + R(T::a43) * P3y), F4x, F4y);
+    // stage 5
+    const R P5x = P1x + h * (R(T::a51) * F1x + R(T::a52) * F2x + R(T::a53) * F3x + R(T::a54) * F4x);
+    const R P5y = P1y + h * (R(T::a51) * F1y + R(T::a52) * F2y + R(T::a53) * F3y + R(T::a54) * F4y);
+    R F5x, F5y;
+    stage(P5x, P5y, h * (R(T::a51) * P1x + R(T::a52) * P2x + R(T::a53) * P3x + R(T::a54) * P4x),
+          h * (R(T::a51) * P1y + R(T::a52) * P2y + R(T::a53) * P3y + R(T::a54) * P4y), F5x, F5y);
+    // stage 6
+    const R P6x = P1x + h * (R(T::a61) * F1x + R(T::a62) * F2x + R(T::a63) * F3x + R(T::a64) * F4x + R(T::a65) * F5x);
+    const R P6y = P1y + h * (R(T::a61) * F1y + R(T::a62) * F2y + R(T::a63) * F3y + R(T::a64) * F4y + R(T::a65) * F5y);
+    R F6x, F6y;
+    stage(P6x, P6y,
+          h * (R(T::a61) * P1x + R(T::a62) * P2x + R(T::a63) * P3x + R(T::a64) * P4x + R(T::a65) * P5x),
+          h * (R(T::a61) * P1y + R(T::a62) * P2y + R(T::a63) * P3y + R(T::a64) * P4y + R(T::a65) * P5y), F6x, F6y);
+    // fifth-order solution
+    const R dX = h * (R(T::b1) * P1x + R(T::b3) * P3x + R(T::b4) * P4x + R(T::b5) * P5x + R(T::b6) * P6x);
+    const R dY = h * (R(T::b1) * P1y + R(T::b3) * P3y + R(T::b4) * P4y + R(T::b5) * P5y + R(T::b6) * P6y);
+    const R dPx = h * (R(T::b1) * F1x + R(T::b3) * F3x + R(T::b4) * F4x + R(T::b5) * F5x + R(T::b6) * F6x);
+    const R dPy = h * (R(T::b1) * F1y + R(T::b3) * F3y + R(T::b4) * F4y + R(T::b5) * F5y + R(T::b6) * F6y);
+    const R P7x = s.px + dPx, P7y = s.py + dPy;
+    o = s;
+    kahan_add(o.X, o.cX, dX);
+    kahan_add(o.y, o.cy, dY);
+    kahan_add(o.z, o.cz, h * s.pz);
+    kahan_add(o.px, o.cpx, dPx);
+    kahan_add(o.py, o.cpy, dPy);
+    // force at the fifth-order point (first same as last)
+    w0_continue(kA, o.X, o.y, o.X - Xp, o.y - yp, wr, wi, rr, ri, st);
+    o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
+    ray_force(wr, wi, rr, ri, o.Fx, o.Fy);
+    // error estimate h sum (b - b*) k over the seven stages
+    e[0] = h * (R(T::e1) * P1x + R(T::e3) * P3x + R(T::e4) * P4x + R(T::e5) * P5x + R(T::e6) * P6x + R(T::e7) * P7x);
+    e[1] = h * (R(T::e1) * P1y + R(T::e3) * P3y + R(T::e4) * P4y + R(T::e5) * P5y + R(T::e6) * P6y + R(T::e7) * P7y);
+    e[2] = h * (R(T::e1) * F1x + R(T::e3) * F3x + R(T::e4) * F4x + R(T::e5) * F5x + R(T::e6) * F6x + R(T::e7) * o.Fx);
+    e[3] = h * (R(T::e1) * F1y + R(T::e3) * F3y + R(T::e4) * F4y + R(T::e5) * F5y + R(T::e6) * F6y + R(T::e7) * o.Fy);
+    if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
+    else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+}
+
+// One step of the scene's integrator of size h from s into o (for event
+// location: Phi_{theta h}(s) is one step of size theta h).
+template <class R, int INTEG>
+__device__ __forceinline__ void integ_step(R kA, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
+{
+    if constexpr (INTEG == RT_DP45) {
+        R e[4];
+        dp45_step(kA, s, h, o, e, st);
+    } else {
+        rk4_step(kA, s, h, o, st);
+    }
+}
+
 // ------------------------------------------------------------------------
 // Events inside the cloak: positive while the ray is inside, negative once it
 // crossed the grating (v = Im w = y + Re W0/k < 0) or a face of the box.
@@ -260,11 +361,10 @@ __device__ __forceinline__ void face_normal(int ev, R N[3])
 // then Newton steps with the slope at the current point, kept inside the
 // bracket (regula falsi otherwise).  On return t = Phi_{theta h}(b) with W0
 // solved.
-template <class R>
-__device__ R locate_event(const StepConst<R>& k, const Box<R>& b, int ev, bool on_surface, R g1, Box<R>& t,
+template <class R, int INTEG>
+__device__ R locate_event(const StepConst<R>& k, const Box<R>& b, R h, int ev, bool on_surface, R g1, Box<R>& t,
                           LaneStats& st)
 {
-    const R h = k.h;
     const R s0 = event_slope(ev, b, h);
     R lo = R(0), hi = R(1), glo, ghi = g1;
     R th;
@@ -294,7 +394,7 @@ __device__ R locate_event(const StepConst<R>& k, const Box<R>& b, int ev, bool o
     if (!(th > lo && th < hi)) th = R(0.5) * (lo + hi);
     int side = 0;
     for (int it = 0; it < Mth<R>::kEventIt; ++it) {
-        rk4_step(k.kA, b, th * h, t, st);
+        integ_step<R, INTEG>(k.kA, b, th * h, t, st);
         w0_eval(k.kA, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
         const R g = event_g(k, ev, t);
         if (fabs(g) <= Mth<R>::kEventTol) return th;
@@ -647,6 +747,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             b.py = (R)(pt[1] - pin * N[1]);
             b.pz = (R)(pt[2] - pin * N[2]);
             b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
+            b.hc = k.h;
             ray_force(b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy);
             surf = face;
             phase = PH_BOX;
@@ -685,7 +786,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
 // ------------------------------------------------------------------------
 // Service of a lane whose step crossed a surface (or hit a guard).
 // ------------------------------------------------------------------------
-template <class R>
+template <class R, int INTEG>
 __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
                               rt_ray_record* rec, LaneStats& st)
 {
@@ -708,16 +809,18 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     Box<R> t;
     for (int ev = 0; ev < EV_COUNT; ++ev) {
         if (C.g1[ev] < R(0)) {
-            const R th = locate_event(k, b, ev, surf == ev, C.g1[ev], t, st);
+            const R th = locate_event<R, INTEG>(k, b, C.hs, ev, surf == ev, C.g1[ev], t, st);
             last = ev;
             if (th < th_best) { th_best = th; ev_best = ev; }
         }
     }
     if (last != ev_best) {
-        rk4_step(k.kA, b, th_best * k.h, t, st);
+        integ_step<R, INTEG>(k.kA, b, th_best * C.hs, t, st);
         w0_eval(k.kA, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
     }
+    const R hc = b.hc;
     b = t;
+    b.hc = hc;
     ray_force(b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy);
     C.events++;
     C.nevents++;
@@ -782,7 +885,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
 // ------------------------------------------------------------------------
 // The integration step of the hot loop.
 // ------------------------------------------------------------------------
-template <class R>
+template <class R, int INTEG>
 __device__ __forceinline__ void box_step(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf,
                                          int& steps, LaneStats& st)
 {
@@ -792,11 +895,41 @@ __device__ __forceinline__ void box_step(const DevScene& sc, Cold<R>& C, Box<R>&
         return;
     }
     Box<R> s1;
-    rk4_step(k.kA, b, k.h, s1, st);
-    w0_eval(k.kA, s1.X, s1.y, s1.wr, s1.wi, s1.rr, s1.ri, st);
-    ray_force(s1.wr, s1.wi, s1.rr, s1.ri, s1.Fx, s1.Fy);
-    ++steps;
-    st.steps++;
+    R hs;
+    if constexpr (INTEG == RT_DP45) {
+        // one attempt of an adaptive Dormand-Prince step; a rejected attempt
+        // only shrinks the step
+        hs = b.hc;
+        R e[4];
+        dp45_step(k.kA, b, hs, s1, e, st);
+        ++steps;
+        st.steps++;
+        const R scp = k.atol + k.rtol;                                    // positions (units of Lambda)
+        const R s2 = k.atol + k.rtol * fmax(fabs(b.px), fabs(s1.px));
+        const R s3 = k.atol + k.rtol * fmax(fabs(b.py), fabs(s1.py));
+        const R q0 = e[0] / scp, q1 = e[1] / scp, q2 = e[2] / s2, q3 = e[3] / s3;
+        const R err = Mth<R>::sqrt_(R(0.25) * (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3));
+        R fac = (err > R(0)) ? R(0.9) * pow(err, R(-0.2)) : R(5);
+        fac = fmin(R(5), fmax(R(0.2), fac));
+        if (!(err <= R(1))) {
+            if (!isfinite(err)) {
+                for (int q = 0; q < EV_COUNT; ++q) C.g1[q] = R(NAN);
+                C.hs = hs;
+                phase = PH_EVENT;
+                return;
+            }
+            b.hc = fmin(hs * fmin(fac, R(1)), k.hmax);
+            return;
+        }
+        s1.hc = fmin(hs * fac, k.hmax);
+    } else {
+        hs = k.h;
+        rk4_step(k.kA, b, hs, s1, st);
+        w0_eval(k.kA, s1.X, s1.y, s1.wr, s1.wi, s1.rr, s1.ri, st);
+        ray_force(s1.wr, s1.wi, s1.rr, s1.ri, s1.Fx, s1.Fy);
+        ++steps;
+        st.steps++;
+    }
     const R gG = s1.y + s1.wr * R(kInvTwoPi);
     const R gT = k.ytop - s1.y;
     const R gXp = (k.E2 - s1.cx) - s1.X, gXm = (k.E2 + s1.cx) + s1.X;
@@ -813,6 +946,8 @@ __device__ __forceinline__ void box_step(const DevScene& sc, Cold<R>& C, Box<R>&
     C.g1[EV_XM] = gXm;
     C.g1[EV_ZP] = gZp;
     C.g1[EV_ZM] = gZm;
+    C.hs = hs;
+    if constexpr (INTEG == RT_DP45) b.hc = s1.hc;
     phase = PH_EVENT;
 }
 
@@ -851,7 +986,7 @@ __device__ __forceinline__ uint8_t quantize8(float c)
     return (uint8_t)floorf(v * 255.0f + 0.5f);
 }
 
-template <class R, int MINB>
+template <class R, int MINB, int INTEG>
 __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid_constant__ DevScene sc,
                                                               float* __restrict__ rgb, uint8_t* __restrict__ rgb8,
                                                               rt_ray_record* rec, unsigned long long* counters,
@@ -878,7 +1013,8 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
         // lanes outside the integration catch up until their ray is inside
         // the cloak again or the work is exhausted
         while (phase != PH_BOX && phase != PH_EXIT) {
-            if (phase == PH_EVENT || phase == PH_GUARD) service_event(sc, C, b, phase, surf, steps, rec, st);
+            if (phase == PH_EVENT || phase == PH_GUARD)
+                service_event<R, INTEG>(sc, C, b, phase, surf, steps, rec, st);
             if (phase == PH_IDLE) {
                 const int64_t w = grab_work(&counters[0], lane);
                 if (w >= sc.nwork) { phase = PH_EXIT; break; }
@@ -918,7 +1054,7 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
             prof_iters += 1;
             prof_lanes += __popc(__ballot_sync(0xffffffffu, phase == PH_BOX));
 #endif
-            if (phase == PH_BOX) box_step(sc, C, b, phase, surf, steps, st);
+            if (phase == PH_BOX) box_step<R, INTEG>(sc, C, b, phase, surf, steps, st);
             if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
         }
 #if RT_PROFILE

@@ -344,3 +344,48 @@ def test_xcorr_of_renders(rt, torch, orc):
             j0, j1 = orc.fov_columns(64, 50.0, fov)
             ref = orc.xcorr(refs["mirror"], refs[kind], j0, j1)
             assert np.abs(out[q] - ref).max() < 1e-4 * 30, (kind, fov, out[q], ref)
+
+
+# ---------------------------------------------------------------------------
+# Dormand-Prince RK45 (adaptive steps)
+# ---------------------------------------------------------------------------
+def test_dp45_fp64_matches_oracle(rt, torch, orc):
+    """Same tolerance (1e-7) on both sides: the same step sequence and exit."""
+    p = inputs.base_scene(width=64, height=64, spp=1, integrator=1, rtol=1e-7, atol=1e-7, precision=1)
+    g = gpu_render(rt, torch, p)
+    o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
+    info = compare_records(g["rec"], o_rec, min_frac=1.0)
+    assert info["ddir_max"] < 1e-9
+    compare_images(g["rgb8"], orc.quantize(o_rgb))
+
+
+@pytest.mark.parametrize("rtol", [1e-5, 1e-7])
+def test_dp45_fp32_matches_oracle(rt, torch, orc, rtol):
+    """FP32 against the oracle at the same tolerance, on the rays FP32 can resolve."""
+    p = inputs.base_scene(width=64, height=64, spp=1, integrator=1, rtol=rtol, atol=rtol, precision=0)
+    g = gpu_render(rt, torch, p)
+    o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
+    cond = fp32_resolvable(orc, p, np.arange(64 * 64), 1, o_rec)
+    compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
+    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.002)
+
+
+@pytest.mark.parametrize("extent,A", [(2.0, 0.02), (8.0, 0.04), (32.0, 0.04)])
+def test_hd_workload_sampled(rt, torch, orc, extent, A):
+    """1920 x 1080, 16 samples per pixel, Dormand-Prince, value-noise
+    background: a seeded subset of pixels rendered by rt_render_pixels (the
+    same arithmetic as the full render) against the oracle."""
+    tex = inputs.value_noise(2048, seed=3)
+    p = inputs.config_hd(extent=extent, A=A, precision=0)
+    pix_np = inputs.pixel_subset(1080, 1920, 120, seed=31)
+    sc = rt.Scene(p, tex=tex)
+    pix = torch.tensor(pix_np, dtype=torch.int64, device="cuda")
+    rgb = torch.zeros((pix_np.size, 3), dtype=torch.float32, device="cuda")
+    rec = torch.zeros(pix_np.size * 16 * 80, dtype=torch.uint8, device="cuda")
+    sc.render_pixels(pix, rgb, rec)
+    torch.cuda.synchronize()
+    g = rt.records_to_numpy(rec)
+    o_rgb, o_rec = orc.render_pixels(orc.Scene(p, tex=tex), pix_np, records=True)
+    cond = fp32_resolvable(orc, p, pix_np, 16, o_rec, tex)
+    compare_records(g, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.97)
+    assert np.median(np.abs(rgb.cpu().numpy() - o_rgb)) < 1e-4

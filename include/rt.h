@@ -195,6 +195,54 @@ int rt_scene_set_launch(rt_scene* scene, int32_t variant, int32_t min_active);
 int rt_scene_get_launch(rt_scene* scene, int32_t* variant, int32_t* min_active, int32_t* grid);
 
 /*
+ * rt_scene_autotune: time the scene's launch configurations (every
+ * register-budget variant compiled for its precision and integrator, times
+ * min_active in {12, 16, 20, 24, 28}; median of `trials` full renders into
+ * d_rgb, which must hold one image) and keep the fastest.  The choice is
+ * cached per scene class (precision, integrator, mirror, cloak and the power
+ * of two of width * height * spp) for the process, and in the text file named
+ * by the environment variable RT_AUTOTUNE_CACHE if set; a cached class is not
+ * timed again.  Synchronous.  Outputs (nullable) report the choice.
+ */
+int rt_scene_autotune(rt_scene* scene, float* d_rgb, int32_t trials, void* stream, int32_t* variant,
+                      int32_t* min_active);
+
+/*
+ * Batches: several scenes rendered by one persistent launch whose warps share
+ * one work list, so scenes of uneven size, spp and path length balance on
+ * the GPU.  The scenes must share precision and integrator, live on the
+ * current device and outlive the batch.  The launch (counter reset and
+ * kernel) is recorded in a CUDA graph by the first rt_batch_render and
+ * replayed by later calls; results equal those of rendering each scene alone.
+ */
+typedef struct rt_batch rt_batch;
+
+/* rt_batch_create: copy the scene tables of scenes[0..n-1] to the device. */
+int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out);
+
+/* rt_batch_destroy: free the batch (waits for its outstanding work). */
+void rt_batch_destroy(rt_batch* batch);
+
+/*
+ * rt_batch_render: render every scene of the batch; d_rgb is a host array of
+ * n device pointers, d_rgb[i] receiving scene i's height x width_out x 3
+ * float image.  Asynchronous on `stream` (a change of output pointers
+ * uploads the new table first, synchronously).
+ */
+int rt_batch_render(rt_batch* batch, float* const* d_rgb, void* stream);
+
+/* rt_batch_stats: counters of the last batch render, summed over its scenes. */
+int rt_batch_stats(rt_batch* batch, rt_stats* out);
+
+/* rt_batch_set_launch / rt_batch_get_launch: min_active of the batch kernel
+   (1..32), its grid and the total number of pixels. */
+int rt_batch_set_launch(rt_batch* batch, int32_t min_active);
+int rt_batch_get_launch(rt_batch* batch, int32_t* min_active, int32_t* grid, int64_t* total_pixels);
+
+/* rt_batch_autotune: as rt_scene_autotune for the batch kernel (min_active). */
+int rt_batch_autotune(rt_batch* batch, float* const* d_rgb, int32_t trials, void* stream, int32_t* min_active);
+
+/*
  * rt_xcorr: image cross-correlation C(0,0) of Eqs. 14-15 (Sec. 5) between
  * the reference d_f and d_g (both height x width x channels float, device).
  * For each of the n_fov fields of view fov_deg[q] (host array, degrees) the

@@ -1,5 +1,6 @@
 // rt_api.cu -- host runtime behind the C ABI of include/rt.h: descriptor
 // validation, scene tables on the device, launches, counters and errors.
+#include <algorithm>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -182,6 +183,32 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->two_over_h = 2.0 / (double)d->height;
 }
 
+namespace grt {
+
+int scene_info(rt_scene* s, DevScene* dev, int* precision, int* integrator, int* device)
+{
+    if (!s) { set_error("scene is NULL"); return RT_EINVAL; }
+    *dev = s->dev;
+    *precision = s->desc.precision;
+    *integrator = s->desc.integrator;
+    *device = s->device;
+    return RT_OK;
+}
+
+void counters_to_stats(const unsigned long long* c, rt_stats* out)
+{
+    out->rays = c[1];
+    out->steps = c[2];
+    out->evals = c[3];
+    out->newton = c[4];
+    out->events = c[5];
+    out->fp64_refine = c[6];
+    for (int q = 0; q < 5; ++q) out->status[q] = c[7 + q];
+    for (int q = 0; q < 4; ++q) out->profile[q] = c[12 + q];
+}
+
+}  // namespace grt
+
 extern "C" {
 
 const char* rt_last_error(void) { return g_err; }
@@ -304,14 +331,60 @@ int rt_scene_stats(rt_scene* s, rt_stats* out)
     unsigned long long c[kCounters];
     RT_CK(cudaEventSynchronize(s->done));
     RT_CK(cudaMemcpy(c, s->d_counters, sizeof c, cudaMemcpyDeviceToHost));
-    out->rays = c[1];
-    out->steps = c[2];
-    out->evals = c[3];
-    out->newton = c[4];
-    out->events = c[5];
-    out->fp64_refine = c[6];
-    for (int q = 0; q < 5; ++q) out->status[q] = c[7 + q];
-    for (int q = 0; q < 4; ++q) out->profile[q] = c[12 + q];
+    counters_to_stats(c, out);
+    return RT_OK;
+}
+
+int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, int32_t* variant_out,
+                      int32_t* min_active_out)
+{
+    g_err[0] = 0;
+    RT_REQ(s && d_rgb, "scene and d_rgb must not be NULL");
+    RT_REQ(trials >= 1 && trials <= 64, "trials must be 1..64");
+    const rt_scene_desc& d = s->desc;
+    // scenes of one class share a configuration: precision, integrator,
+    // cloak and the power of two of the number of samples
+    const double samples = (double)s->dev.nwork * d.spp;
+    char key[160];
+    snprintf(key, sizeof key, "scene/p%d/i%d/c%d/m%d/log2n%d", d.precision, d.integrator, d.cloak, d.mirror,
+             (int)floor(log2(samples > 1.0 ? samples : 1.0)));
+    int v = kDefaultVariant, m = kMinActive;
+    if (!tune_lookup(key, &v, &m)) {
+        const int nvar = (d.precision == RT_FP32 && d.integrator == RT_RK4) ? kVariants : 1;
+        const int cand[] = {12, 16, 20, 24, 28};
+        cudaStream_t st = (cudaStream_t)stream;
+        cudaEvent_t e0, e1;
+        RT_CK(cudaEventCreate(&e0));
+        RT_CK(cudaEventCreate(&e1));
+        float best = 1e30f;
+        int rc = RT_OK;
+        for (int var = 0; var < nvar && rc == RT_OK; ++var) {
+            for (int c : cand) {
+                rc = rt_scene_set_launch(s, var, c);
+                if (rc != RT_OK) break;
+                rc = render_common(s, nullptr, s->dev.nwork, d_rgb, nullptr, nullptr, stream);   // warm-up
+                float t[64];
+                for (int k = 0; rc == RT_OK && k < trials; ++k) {
+                    cudaEventRecord(e0, st);
+                    rc = render_common(s, nullptr, s->dev.nwork, d_rgb, nullptr, nullptr, stream);
+                    cudaEventRecord(e1, st);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&t[k], e0, e1);
+                }
+                if (rc != RT_OK) break;
+                std::sort(t, t + trials);
+                if (t[trials / 2] < best) { best = t[trials / 2]; v = var; m = c; }
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        if (rc != RT_OK) return rc;
+        tune_record(key, v, m);
+    }
+    const int rc = rt_scene_set_launch(s, v, m);
+    if (rc != RT_OK) return rc;
+    if (variant_out) *variant_out = v;
+    if (min_active_out) *min_active_out = m;
     return RT_OK;
 }
 

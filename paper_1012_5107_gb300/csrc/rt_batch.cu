@@ -1,0 +1,323 @@
+// rt_batch.cu -- many scenes in one persistent launch replayed from a CUDA
+// graph, and the autotuner of the launch configuration.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "rt_internal.h"
+#include "rt_trace.cuh"
+
+namespace grt {
+
+template <class R, int INTEG>
+static cudaError_t batch_occupancy_t(int* bps)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_batch_kernel<R, INTEG>, kRenderBlock, 0);
+}
+
+cudaError_t batch_occupancy(int precision, int integrator, int* bps)
+{
+    if (precision == RT_FP64)
+        return integrator == RT_DP45 ? batch_occupancy_t<double, RT_DP45>(bps) : batch_occupancy_t<double, RT_RK4>(bps);
+    return integrator == RT_DP45 ? batch_occupancy_t<float, RT_DP45>(bps) : batch_occupancy_t<float, RT_RK4>(bps);
+}
+
+cudaError_t launch_batch(int precision, int integrator, const DevScene* scenes, const int64_t* offsets,
+                         float* const* rgbs, int n, int64_t total, unsigned long long* counters, int min_active,
+                         int grid, cudaStream_t stream)
+{
+    if (precision == RT_FP64) {
+        if (integrator == RT_DP45)
+            render_batch_kernel<double, RT_DP45><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
+                                                                                   counters, min_active);
+        else
+            render_batch_kernel<double, RT_RK4><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
+                                                                                  counters, min_active);
+    } else {
+        if (integrator == RT_DP45)
+            render_batch_kernel<float, RT_DP45><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
+                                                                                  counters, min_active);
+        else
+            render_batch_kernel<float, RT_RK4><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
+                                                                                 counters, min_active);
+    }
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------
+// Autotuner cache: key -> (variant, min_active), for the process and
+// optionally in the text file named by RT_AUTOTUNE_CACHE ("key variant
+// min_active" per line).
+// ------------------------------------------------------------------------
+static std::mutex g_tune_mutex;
+static std::map<std::string, std::pair<int, int>> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load_locked()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    const char* path = getenv("RT_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "r");
+    if (!f) return;
+    char key[256];
+    int v, m;
+    while (fscanf(f, "%255s %d %d", key, &v, &m) == 3) g_tune[key] = {v, m};
+    fclose(f);
+}
+
+static void tune_store_locked()
+{
+    const char* path = getenv("RT_AUTOTUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    for (const auto& kv : g_tune) fprintf(f, "%s %d %d\n", kv.first.c_str(), kv.second.first, kv.second.second);
+    fclose(f);
+}
+
+bool tune_lookup(const std::string& key, int* variant, int* min_active)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it == g_tune.end()) return false;
+    *variant = it->second.first;
+    *min_active = it->second.second;
+    return true;
+}
+
+void tune_record(const std::string& key, int variant, int min_active)
+{
+    std::lock_guard<std::mutex> lock(g_tune_mutex);
+    tune_load_locked();
+    g_tune[key] = {variant, min_active};
+    tune_store_locked();
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+#define RT_CK(call)                                                                                   \
+    do {                                                                                              \
+        cudaError_t e_ = (call);                                                                      \
+        if (e_ != cudaSuccess) {                                                                      \
+            set_error("%s:%d: %s: %s", __FILE__, __LINE__, #call, cudaGetErrorString(e_));            \
+            return RT_ECUDA;                                                                          \
+        }                                                                                             \
+    } while (0)
+
+#define RT_REQ(cond, ...)                                                                             \
+    do {                                                                                              \
+        if (!(cond)) {                                                                                \
+            set_error(__VA_ARGS__);                                                                   \
+            return RT_EINVAL;                                                                         \
+        }                                                                                             \
+    } while (0)
+
+struct rt_batch {
+    int n, device, precision, integrator, grid, nsm, min_active;
+    int64_t total;
+    DevScene* d_scenes;
+    int64_t* d_offsets;
+    float** d_rgbs;
+    std::vector<float*> h_rgbs;        // output pointers last uploaded
+    unsigned long long* d_counters;
+    cudaGraph_t graph;
+    cudaGraphExec_t exec;
+    int graph_min_active;
+    cudaEvent_t done;
+};
+
+extern "C" {
+
+int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
+{
+    RT_REQ(out, "out is NULL");
+    *out = nullptr;
+    RT_REQ(scenes && n >= 1, "need at least one scene");
+    std::vector<DevScene> dev(n);
+    std::vector<int64_t> off(n + 1, 0);
+    int precision = -1, integrator = -1, device = -1;
+    for (int i = 0; i < n; ++i) {
+        RT_REQ(scenes[i], "scene %d is NULL", i);
+        int p, g, d;
+        if (scene_info(scenes[i], &dev[i], &p, &g, &d) != RT_OK) return RT_EINVAL;
+        RT_REQ(dev[i].pix_list == nullptr, "scene %d", i);
+        if (i == 0) { precision = p; integrator = g; device = d; }
+        RT_REQ(p == precision && g == integrator, "scenes of a batch must share precision and integrator (scene %d)", i);
+        RT_REQ(d == device, "scenes of a batch must live on one device (scene %d)", i);
+        off[i + 1] = off[i] + dev[i].nwork;
+    }
+    int cur = -1;
+    RT_CK(cudaGetDevice(&cur));
+    RT_REQ(cur == device, "current device %d, scenes live on device %d", cur, device);
+    rt_batch* b = new (std::nothrow) rt_batch();
+    if (!b) { set_error("host allocation failed"); return RT_ENOMEM; }
+    b->n = n;
+    b->device = device;
+    b->precision = precision;
+    b->integrator = integrator;
+    b->total = off[n];
+    b->min_active = kMinActive;
+    b->graph_min_active = -1;
+    b->h_rgbs.assign(n, nullptr);
+    cudaError_t e = cudaMalloc(&b->d_scenes, sizeof(DevScene) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_offsets, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_rgbs, sizeof(float*) * n);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned long long) * kCounters);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_scenes, dev.data(), sizeof(DevScene) * n, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_offsets, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(b->d_rgbs, 0, sizeof(float*) * n);
+    if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned long long) * kCounters);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+    int bps = 0;
+    if (e == cudaSuccess) e = batch_occupancy(precision, integrator, &bps);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, device);
+    if (e != cudaSuccess) {
+        set_error("rt_batch_create: %s", cudaGetErrorString(e));
+        rt_batch_destroy(b);
+        return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+    }
+    b->grid = (bps > 0 ? bps : 1) * b->nsm;
+    *out = b;
+    return RT_OK;
+}
+
+void rt_batch_destroy(rt_batch* b)
+{
+    if (!b) return;
+    if (b->done) cudaEventSynchronize(b->done);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->d_scenes) cudaFree(b->d_scenes);
+    if (b->d_offsets) cudaFree(b->d_offsets);
+    if (b->d_rgbs) cudaFree(b->d_rgbs);
+    if (b->d_counters) cudaFree(b->d_counters);
+    if (b->done) cudaEventDestroy(b->done);
+    delete b;
+}
+
+int rt_batch_render(rt_batch* b, float* const* d_rgb, void* stream)
+{
+    RT_REQ(b && d_rgb, "batch and d_rgb must not be NULL");
+    for (int i = 0; i < b->n; ++i) RT_REQ(d_rgb[i], "d_rgb[%d] is NULL", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    // a change of output images is a small upload outside the graph
+    bool changed = false;
+    for (int i = 0; i < b->n; ++i) changed = changed || (b->h_rgbs[i] != d_rgb[i]);
+    if (changed) {
+        for (int i = 0; i < b->n; ++i) b->h_rgbs[i] = d_rgb[i];
+        RT_CK(cudaMemcpyAsync(b->d_rgbs, b->h_rgbs.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice, st));
+        RT_CK(cudaStreamSynchronize(st));
+    }
+    if (!b->exec || b->graph_min_active != b->min_active) {
+        if (b->exec) { cudaGraphExecDestroy(b->exec); b->exec = nullptr; }
+        if (b->graph) { cudaGraphDestroy(b->graph); b->graph = nullptr; }
+        // record the launch (counter reset and the persistent kernel) once
+        cudaStream_t cap;
+        RT_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * kCounters, cap);
+        if (e == cudaSuccess)
+            e = launch_batch(b->precision, b->integrator, b->d_scenes, b->d_offsets, b->d_rgbs, b->n, b->total,
+                             b->d_counters, b->min_active, b->grid, cap);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        RT_CK(e);
+        RT_CK(e2);
+        b->graph = g;
+        RT_CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+        b->graph_min_active = b->min_active;
+    }
+    RT_CK(cudaGraphLaunch(b->exec, st));
+    RT_CK(cudaEventRecord(b->done, st));
+    return RT_OK;
+}
+
+int rt_batch_stats(rt_batch* b, rt_stats* out)
+{
+    RT_REQ(b && out, "batch and out must not be NULL");
+    unsigned long long c[kCounters];
+    RT_CK(cudaEventSynchronize(b->done));
+    RT_CK(cudaMemcpy(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost));
+    counters_to_stats(c, out);
+    return RT_OK;
+}
+
+int rt_batch_set_launch(rt_batch* b, int32_t min_active)
+{
+    RT_REQ(b, "batch is NULL");
+    RT_REQ(min_active >= 1 && min_active <= 32, "min_active must be 1..32");
+    b->min_active = min_active;
+    return RT_OK;
+}
+
+int rt_batch_get_launch(rt_batch* b, int32_t* min_active, int32_t* grid, int64_t* total)
+{
+    RT_REQ(b, "batch is NULL");
+    if (min_active) *min_active = b->min_active;
+    if (grid) *grid = b->grid;
+    if (total) *total = b->total;
+    return RT_OK;
+}
+
+// Time one configuration: median of `trials` renders (after one warm-up).
+static int time_batch(rt_batch* b, float* const* d_rgb, cudaStream_t st, int trials, float* ms)
+{
+    cudaEvent_t e0, e1;
+    RT_CK(cudaEventCreate(&e0));
+    RT_CK(cudaEventCreate(&e1));
+    std::vector<float> t;
+    int rc = rt_batch_render(b, d_rgb, st);
+    for (int k = 0; rc == RT_OK && k < trials; ++k) {
+        cudaEventRecord(e0, st);
+        rc = rt_batch_render(b, d_rgb, st);
+        cudaEventRecord(e1, st);
+        cudaEventSynchronize(e1);
+        float x = 0.0f;
+        cudaEventElapsedTime(&x, e0, e1);
+        t.push_back(x);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != RT_OK) return rc;
+    std::sort(t.begin(), t.end());
+    *ms = t[t.size() / 2];
+    return RT_OK;
+}
+
+int rt_batch_autotune(rt_batch* b, float* const* d_rgb, int32_t trials, void* stream, int32_t* min_active_out)
+{
+    RT_REQ(b && d_rgb, "batch and d_rgb must not be NULL");
+    RT_REQ(trials >= 1 && trials <= 64, "trials must be 1..64");
+    char key[128];
+    snprintf(key, sizeof key, "batch/p%d/i%d/n%d", b->precision, b->integrator, b->n);
+    int v = 0, m = 0;
+    if (!tune_lookup(key, &v, &m)) {
+        const int cand[] = {12, 16, 20, 24, 28};
+        float best = 1e30f;
+        m = kMinActive;
+        for (int c : cand) {
+            b->min_active = c;
+            float ms = 0.0f;
+            const int rc = time_batch(b, d_rgb, (cudaStream_t)stream, trials, &ms);
+            if (rc != RT_OK) return rc;
+            if (ms < best) { best = ms; m = c; }
+        }
+        tune_record(key, 0, m);
+    }
+    b->min_active = m;
+    if (min_active_out) *min_active_out = m;
+    return RT_OK;
+}
+
+}  // extern "C"

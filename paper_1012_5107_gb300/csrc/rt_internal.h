@@ -45,3 +45,20 @@ void fov_windows(int W, double hfov_deg, const double* fov_deg, int n_fov, Windo
 void set_error(const char* fmt, ...);
 
 }  // namespace grt
+
+struct rt_scene;
+
+namespace grt {
+
+// Scene table, precision, integrator and device of a scene.
+int scene_info(rt_scene* s, DevScene* dev, int* precision, int* integrator, int* device);
+void counters_to_stats(const unsigned long long* c, rt_stats* out);
+
+// Autotuner cache (process lifetime, optionally the RT_AUTOTUNE_CACHE file).
+}  // namespace grt
+#include <string>
+namespace grt {
+bool tune_lookup(const std::string& key, int* variant, int* min_active);
+void tune_record(const std::string& key, int variant, int min_active);
+
+}  // namespace grt

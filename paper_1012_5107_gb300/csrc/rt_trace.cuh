@@ -62,8 +62,9 @@ struct Cold {
     R dx, dy, dz;             // air: unit direction
     R g1[EV_COUNT];           // event functions at the end of a step that crossed a surface
     R hs;                     // size of that step
-    int64_t work;             // work item (pixel slot)
+    int64_t work;             // output slot of the pixel in its scene's arrays
     int64_t pix;              // pixel index i*wout + j
+    int scene;                // scene of the pixel (batched renders)
     float acc[3], col[3];
     int sample, bounces, events, status;
     uint32_t rays, nevents, stat[5];
@@ -986,21 +987,66 @@ __device__ __forceinline__ uint8_t quantize8(float c)
     return (uint8_t)floorf(v * 255.0f + 0.5f);
 }
 
-template <class R, int MINB, int INTEG>
-__global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid_constant__ DevScene sc,
-                                                              float* __restrict__ rgb, uint8_t* __restrict__ rgb8,
-                                                              rt_ray_record* rec, unsigned long long* counters,
-                                                              int min_active)
+// Where the work of a launch comes from: one scene (constants in the kernel
+// parameters) or a table of scenes whose pixels are numbered one after the
+// other (constants in device memory).
+struct OneScene {
+    const DevScene& sc;
+    float* rgb;
+    uint8_t* rgb8;
+    rt_ray_record* rec;
+    __device__ __forceinline__ const DevScene& scene(int) const { return sc; }
+    __device__ __forceinline__ int64_t nwork() const { return sc.nwork; }
+    __device__ __forceinline__ void map(int64_t w, int& s, int64_t& pix, int64_t& out) const
+    {
+        s = 0;
+        out = w;
+        pix = sc.pix_list ? sc.pix_list[w] : w;
+    }
+    __device__ __forceinline__ float* rgb_of(int) const { return rgb; }
+    __device__ __forceinline__ uint8_t* rgb8_of(int) const { return rgb8; }
+    __device__ __forceinline__ rt_ray_record* rec_of(int) const { return rec; }
+};
+
+struct ManyScenes {
+    const DevScene* scenes;
+    const int64_t* offsets;          // n + 1 entries: first work item of each scene
+    float* const* rgbs;              // per-scene output images
+    int n;
+    int64_t total;
+    __device__ __forceinline__ const DevScene& scene(int s) const { return scenes[s]; }
+    __device__ __forceinline__ int64_t nwork() const { return total; }
+    __device__ __forceinline__ void map(int64_t w, int& s, int64_t& pix, int64_t& out) const
+    {
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {                 // last scene whose first item is <= w
+            const int mid = (lo + hi + 1) >> 1;
+            if (__ldg(offsets + mid) <= w) lo = mid;
+            else hi = mid - 1;
+        }
+        s = lo;
+        out = pix = w - __ldg(offsets + lo);
+    }
+    __device__ __forceinline__ float* rgb_of(int s) const { return rgbs[s]; }
+    __device__ __forceinline__ uint8_t* rgb8_of(int) const { return nullptr; }
+    __device__ __forceinline__ rt_ray_record* rec_of(int) const { return nullptr; }
+};
+
+// The persistent render loop of one thread (see the top of this file).
+template <class R, int INTEG, class Src>
+__device__ __forceinline__ void render_loop(const Src& src, unsigned long long* counters, int min_active)
 {
     __shared__ Cold<R> cold_all[kRenderBlock];
     Cold<R>& C = cold_all[threadIdx.x];
     C.rays = 0;
     C.nevents = 0;
+    C.scene = 0;
     for (int q = 0; q < 5; ++q) C.stat[q] = 0;
     Box<R> b;
     int phase = PH_IDLE, surf = EV_NONE, steps = 0;
     LaneStats st = {0u, 0u, 0u, 0u};
     const unsigned lane = threadIdx.x & 31u;
+    const int64_t nwork = src.nwork();
 #if RT_PROFILE
     // per-warp cycle split (lane 0): service pass, integration loop, loop
     // iterations and lanes inside the cloak summed over those iterations
@@ -1014,17 +1060,22 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
         // the cloak again or the work is exhausted
         while (phase != PH_BOX && phase != PH_EXIT) {
             if (phase == PH_EVENT || phase == PH_GUARD)
-                service_event<R, INTEG>(sc, C, b, phase, surf, steps, rec, st);
+                service_event<R, INTEG>(src.scene(C.scene), C, b, phase, surf, steps, src.rec_of(C.scene), st);
             if (phase == PH_IDLE) {
                 const int64_t w = grab_work(&counters[0], lane);
-                if (w >= sc.nwork) { phase = PH_EXIT; break; }
-                C.work = w;
-                C.pix = sc.pix_list ? sc.pix_list[w] : w;
+                if (w >= nwork) { phase = PH_EXIT; break; }
+                int s;
+                int64_t pix, out;
+                src.map(w, s, pix, out);
+                C.scene = s;
+                C.work = out;
+                C.pix = pix;
                 C.sample = 0;
                 C.acc[0] = C.acc[1] = C.acc[2] = 0.0f;
-                start_sample(sc, C, phase, surf, steps);
+                start_sample(src.scene(s), C, phase, surf, steps);
             }
-            if (phase == PH_AIR) air_segment(sc, C, b, phase, surf, steps, rec, st);
+            const DevScene& sc = src.scene(C.scene);
+            if (phase == PH_AIR) air_segment(sc, C, b, phase, surf, steps, src.rec_of(C.scene), st);
             if (phase == PH_DONE) {
                 if (++C.sample < sc.spp) {
                     start_sample(sc, C, phase, surf, steps);
@@ -1032,10 +1083,11 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
                     const float inv = 1.0f / (float)sc.spp;
                     float c[3];
                     for (int a = 0; a < 3; ++a) c[a] = C.acc[a] * inv;
-                    float* o = rgb + 3 * C.work;
+                    float* o = src.rgb_of(C.scene) + 3 * C.work;
                     o[0] = c[0]; o[1] = c[1]; o[2] = c[2];
-                    if (rgb8) {
-                        uint8_t* q = rgb8 + 3 * C.work;
+                    uint8_t* q8 = src.rgb8_of(C.scene);
+                    if (q8) {
+                        uint8_t* q = q8 + 3 * C.work;
                         q[0] = quantize8(c[0]); q[1] = quantize8(c[1]); q[2] = quantize8(c[2]);
                     }
                     phase = PH_IDLE;
@@ -1054,7 +1106,7 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
             prof_iters += 1;
             prof_lanes += __popc(__ballot_sync(0xffffffffu, phase == PH_BOX));
 #endif
-            if (phase == PH_BOX) box_step<R, INTEG>(sc, C, b, phase, surf, steps, st);
+            if (phase == PH_BOX) box_step<R, INTEG>(src.scene(C.scene), C, b, phase, surf, steps, st);
             if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
         }
 #if RT_PROFILE
@@ -1079,6 +1131,27 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
         if (lane == 0 && x) atomicAdd(&counters[1 + q], x);
     }
+}
+
+template <class R, int MINB, int INTEG>
+__global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid_constant__ DevScene sc,
+                                                                    float* __restrict__ rgb,
+                                                                    uint8_t* __restrict__ rgb8, rt_ray_record* rec,
+                                                                    unsigned long long* counters, int min_active)
+{
+    const OneScene src{sc, rgb, rgb8, rec};
+    render_loop<R, INTEG>(src, counters, min_active);
+}
+
+// Many scenes in one launch (same precision and integrator): their pixels
+// form one work list, so the warps balance across scenes of uneven size.
+template <class R, int INTEG>
+__global__ void __launch_bounds__(kRenderBlock, kVariantBlocks[0]) render_batch_kernel(
+    const DevScene* __restrict__ scenes, const int64_t* __restrict__ offsets, float* const* __restrict__ rgbs, int n,
+    int64_t total, unsigned long long* counters, int min_active)
+{
+    const ManyScenes src{scenes, offsets, rgbs, n, total};
+    render_loop<R, INTEG>(src, counters, min_active);
 }
 
 // W0, n and the force at arbitrary points.

@@ -67,8 +67,10 @@ class Stats(C.Structure):
 _lib = None
 
 EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels", "rt_render_host",
-           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_xcorr", "rt_xcorr_noalloc",
-           "rt_eval_medium", "rt_last_error", "rt_version"]
+           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_scene_autotune",
+           "rt_batch_create", "rt_batch_destroy", "rt_batch_render", "rt_batch_stats", "rt_batch_set_launch",
+           "rt_batch_get_launch", "rt_batch_autotune",
+           "rt_xcorr", "rt_xcorr_noalloc", "rt_eval_medium", "rt_last_error", "rt_version"]
 
 
 def lib() -> C.CDLL:
@@ -90,6 +92,15 @@ def lib() -> C.CDLL:
     L.rt_scene_stats.argtypes = [vp, C.POINTER(Stats)]
     L.rt_scene_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
     L.rt_scene_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.rt_scene_autotune.argtypes = [vp, vp, C.c_int32, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.rt_batch_create.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(vp)]
+    L.rt_batch_destroy.argtypes = [vp]
+    L.rt_batch_destroy.restype = None
+    L.rt_batch_render.argtypes = [vp, C.POINTER(vp), vp]
+    L.rt_batch_stats.argtypes = [vp, C.POINTER(Stats)]
+    L.rt_batch_set_launch.argtypes = [vp, C.c_int32]
+    L.rt_batch_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
+    L.rt_batch_autotune.argtypes = [vp, C.POINTER(vp), C.c_int32, vp, C.POINTER(C.c_int32)]
     L.rt_xcorr.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                            C.c_double, vp, vp]
     L.rt_xcorr_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
@@ -188,11 +199,69 @@ class Scene:
         _check(lib().rt_scene_get_launch(self._h, C.byref(v), C.byref(m), C.byref(g)))
         return {"variant": v.value, "min_active": m.value, "grid": g.value}
 
+    def autotune(self, rgb, trials: int = 3, stream=None) -> dict:
+        """rt_scene_autotune: time the launch configurations on this scene (rendering into rgb)."""
+        v, m = C.c_int32(), C.c_int32()
+        _check(lib().rt_scene_autotune(self._h, _ptr(rgb), trials, _stream(stream), C.byref(v), C.byref(m)))
+        return {"variant": v.value, "min_active": m.value}
+
     def stats(self) -> dict:
         s = Stats()
         _check(lib().rt_scene_stats(self._h, C.byref(s)))
-        return {"rays": s.rays, "steps": s.steps, "evals": s.evals, "newton": s.newton, "events": s.events,
-                "fp64_refine": s.fp64_refine, "status": list(s.status), "profile": list(s.profile)}
+        return _stats_dict(s)
+
+
+def _stats_dict(s: Stats) -> dict:
+    return {"rays": s.rays, "steps": s.steps, "evals": s.evals, "newton": s.newton, "events": s.events,
+            "fp64_refine": s.fp64_refine, "status": list(s.status), "profile": list(s.profile)}
+
+
+class Batch:
+    """Several scenes rendered by one persistent launch (rt_batch_*); the scenes
+    must stay alive while the batch is used."""
+
+    def __init__(self, scenes: list):
+        self.scenes = list(scenes)
+        arr = (C.c_void_p * len(self.scenes))(*[sc._h.value for sc in self.scenes])
+        h = C.c_void_p()
+        _check(lib().rt_batch_create(arr, len(self.scenes), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _outs(self, outs):
+        assert len(outs) == len(self.scenes)
+        return (C.c_void_p * len(outs))(*[_ptr(t) for t in outs])
+
+    def render(self, outs, stream=None):
+        _check(lib().rt_batch_render(self._h, self._outs(outs), _stream(stream)))
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(lib().rt_batch_stats(self._h, C.byref(s)))
+        return _stats_dict(s)
+
+    def set_launch(self, min_active: int):
+        _check(lib().rt_batch_set_launch(self._h, min_active))
+
+    def get_launch(self) -> dict:
+        m, g, t = C.c_int32(), C.c_int32(), C.c_int64()
+        _check(lib().rt_batch_get_launch(self._h, C.byref(m), C.byref(g), C.byref(t)))
+        return {"min_active": m.value, "grid": g.value, "pixels": t.value}
+
+    def autotune(self, outs, trials: int = 3, stream=None) -> int:
+        m = C.c_int32()
+        _check(lib().rt_batch_autotune(self._h, self._outs(outs), trials, _stream(stream), C.byref(m)))
+        return m.value
 
 
 def records_to_numpy(rec_bytes) -> np.ndarray:

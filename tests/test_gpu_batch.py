@@ -1,0 +1,89 @@
+"""Batched renders (many scenes, one persistent launch replayed from a CUDA
+graph) and the autotuner: results equal those of each scene rendered alone."""
+import numpy as np
+import pytest
+
+from paper_1012_5107_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_5107_gb300 import build as B
+    B.build()
+    from paper_1012_5107_gb300 import rt as r
+    r.lib()
+    return r
+
+
+def small_batch(count, seed, precision=0, integrator=0):
+    """Scenes drawn like the 64-scene batch workload, at small sizes."""
+    out = []
+    for p in inputs.batch_scenes(count=count, seed=seed, precision=precision):
+        side = {128: 24, 256: 32, 512: 40, 1024: 48}[p["width"]]
+        q = dict(p, width=side, height=side - 4, integrator=integrator)
+        if integrator == 1:
+            q.update(rtol=1e-5, atol=1e-5 * q["Lambda"])
+        out.append(q)
+    return out
+
+
+@pytest.mark.parametrize("precision,integrator", [(0, 0), (1, 0), (0, 1)])
+def test_batch_equals_single_renders(rt, precision, integrator):
+    import torch
+    params = small_batch(6, seed=4, precision=precision, integrator=integrator)
+    scenes = [rt.Scene(p) for p in params]
+    singles = []
+    for sc in scenes:
+        img = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+        sc.render(img)
+        singles.append(img)
+    torch.cuda.synchronize()
+    batch = rt.Batch(scenes)
+    outs = [torch.full(sc.shape, -1.0, dtype=torch.float32, device="cuda") for sc in scenes]
+    batch.render(outs)
+    torch.cuda.synchronize()
+    for a, b in zip(singles, outs):
+        assert torch.equal(a, b)
+    st = batch.stats()
+    assert st["rays"] == sum(p["width"] * p["height"] * p["spp"] for p in params)
+    # graph replay with new output buffers gives the same images again
+    outs2 = [torch.zeros_like(o) for o in outs]
+    batch.render(outs2)
+    batch.render(outs2)
+    torch.cuda.synchronize()
+    for a, b in zip(singles, outs2):
+        assert torch.equal(a, b)
+    batch.close()
+
+
+def test_autotune_keeps_results(rt):
+    import torch
+    p = inputs.base_scene(width=96, height=80, spp=4, seed=6, precision=0)
+    sc = rt.Scene(p)
+    ref = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+    sc.render(ref)
+    scratch = torch.zeros_like(ref)
+    choice = sc.autotune(scratch, trials=1)
+    assert 0 <= choice["variant"] < 3 and 12 <= choice["min_active"] <= 28
+    assert sc.get_launch()["min_active"] == choice["min_active"]
+    out = torch.zeros_like(ref)
+    sc.render(out)
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref)
+    # the class is cached: a second scene of the same class gets the same choice
+    sc2 = rt.Scene(dict(p, seed=7))
+    assert sc2.autotune(torch.zeros_like(ref), trials=1) == choice
+
+
+def test_batch_autotune(rt):
+    import torch
+    scenes = [rt.Scene(p) for p in small_batch(4, seed=9)]
+    batch = rt.Batch(scenes)
+    outs = [torch.zeros(sc.shape, dtype=torch.float32, device="cuda") for sc in scenes]
+    m = batch.autotune(outs, trials=1)
+    assert 12 <= m <= 28 and batch.get_launch()["min_active"] == m

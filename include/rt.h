@@ -242,6 +242,57 @@ int rt_batch_get_launch(rt_batch* batch, int32_t* min_active, int32_t* grid, int
 /* rt_batch_autotune: as rt_scene_autotune for the batch kernel (min_active). */
 int rt_batch_autotune(rt_batch* batch, float* const* d_rgb, int32_t trials, void* stream, int32_t* min_active);
 
+/* rt_validate_desc: check a descriptor on the host (no device needed);
+   RT_OK or RT_EINVAL with the offending field in rt_last_error(). */
+int rt_validate_desc(const rt_scene_desc* desc);
+
+/*
+ * Serving: rt_submit queues a render request; a worker thread admits queued
+ * requests in arrival order while the sum of their ray-state footprints
+ * (64 bytes per sample plus the float output image) stays within the budget,
+ * groups the newly admitted requests that share precision and integrator
+ * into one batch launch and runs it on a free stream (at most max_inflight
+ * batches in flight).  Requests that arrive while batches run are admitted as
+ * budget and streams free up; their work overlaps on the device.  Each
+ * result equals a render of the scene alone.  Device allocations of a batch
+ * are stream-ordered on its stream.
+ */
+typedef struct rt_server rt_server;
+
+typedef struct rt_result {
+    int32_t status;           /* RT_OK or the error of the request           */
+    float latency_ms;         /* submission to completion                     */
+    float queue_ms;           /* submission to launch                         */
+    uint64_t rays;            /* camera samples of the request                */
+} rt_result;
+
+typedef struct rt_server_info {
+    uint64_t queued, in_flight, completed, failed;
+    uint64_t bytes_in_use, budget;
+} rt_server_info;
+
+/* rt_server_create: server on the current device; max_inflight 1..16. */
+int rt_server_create(size_t ray_state_budget_bytes, int32_t max_inflight, rt_server** out);
+
+/* rt_server_destroy: fails the requests not yet admitted (RT_ETIMEDOUT),
+   waits for the batches in flight, stops the worker. */
+void rt_server_destroy(rt_server* server);
+
+/* rt_submit: queue a request rendering into d_out (caller-owned device image
+   of height x width_out x 3 floats, untouched until the request completes).
+   RT_EINVAL for an invalid descriptor, RT_EBUSY if the request alone exceeds
+   the budget or the queue is full. */
+int rt_submit(rt_server* server, const rt_scene_desc* desc, float* d_out, uint64_t* ticket);
+
+/* rt_poll: RT_OK (result in *out, the ticket is then forgotten) or the
+   request's error; RT_PENDING if not finished and timeout_us <= 0; waits up
+   to timeout_us microseconds otherwise and returns RT_ETIMEDOUT if still
+   pending. */
+int rt_poll(rt_server* server, uint64_t ticket, int32_t timeout_us, rt_result* out);
+
+/* rt_server_stats: queue and budget state. */
+int rt_server_stats(rt_server* server, rt_server_info* out);
+
 /*
  * rt_xcorr: image cross-correlation C(0,0) of Eqs. 14-15 (Sec. 5) between
  * the reference d_f and d_g (both height x width x channels float, device).

@@ -185,6 +185,8 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
 
 namespace grt {
 
+void build_scene_table(const rt_scene_desc* d, DevScene* s) { build_dev(d, s); }
+
 int scene_info(rt_scene* s, DevScene* dev, int* precision, int* integrator, int* device)
 {
     if (!s) { set_error("scene is NULL"); return RT_EINVAL; }
@@ -212,6 +214,12 @@ void counters_to_stats(const unsigned long long* c, rt_stats* out)
 extern "C" {
 
 const char* rt_last_error(void) { return g_err; }
+
+int rt_validate_desc(const rt_scene_desc* desc)
+{
+    g_err[0] = 0;
+    return validate(desc);
+}
 
 const char* rt_version(void) { return "gratingrt 0.1 (sm_103a)"; }
 

@@ -59,6 +59,12 @@ void counters_to_stats(const unsigned long long* c, rt_stats* out);
 #include <string>
 namespace grt {
 bool tune_lookup(const std::string& key, int* variant, int* min_active);
+// Scene table of a validated descriptor (texture pointer left to the caller).
+void build_scene_table(const rt_scene_desc* d, DevScene* s);
+cudaError_t batch_occupancy(int precision, int integrator, int* bps);
+cudaError_t launch_batch(int precision, int integrator, const DevScene* scenes, const int64_t* offsets,
+                         float* const* rgbs, int n, int64_t total, unsigned long long* counters, int min_active,
+                         int grid, cudaStream_t stream);
 void tune_record(const std::string& key, int variant, int min_active);
 
 }  // namespace grt

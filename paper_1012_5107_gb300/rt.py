@@ -58,6 +58,15 @@ RECORD_DTYPE = np.dtype({
 assert C.sizeof(RayRecord) == RECORD_DTYPE.itemsize
 
 
+class Result(C.Structure):
+    _fields_ = [("status", C.c_int32), ("latency_ms", C.c_float), ("queue_ms", C.c_float), ("rays", C.c_uint64)]
+
+
+class ServerInfo(C.Structure):
+    _fields_ = [("queued", C.c_uint64), ("in_flight", C.c_uint64), ("completed", C.c_uint64),
+                ("failed", C.c_uint64), ("bytes_in_use", C.c_uint64), ("budget", C.c_uint64)]
+
+
 class Stats(C.Structure):
     _fields_ = [("rays", C.c_uint64), ("steps", C.c_uint64), ("evals", C.c_uint64), ("newton", C.c_uint64),
                 ("events", C.c_uint64), ("fp64_refine", C.c_uint64), ("status", C.c_uint64 * 5),
@@ -70,6 +79,7 @@ EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels
            "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_scene_autotune",
            "rt_batch_create", "rt_batch_destroy", "rt_batch_render", "rt_batch_stats", "rt_batch_set_launch",
            "rt_batch_get_launch", "rt_batch_autotune",
+           "rt_validate_desc", "rt_server_create", "rt_server_destroy", "rt_submit", "rt_poll", "rt_server_stats",
            "rt_xcorr", "rt_xcorr_noalloc", "rt_eval_medium", "rt_last_error", "rt_version"]
 
 
@@ -106,6 +116,13 @@ def lib() -> C.CDLL:
     L.rt_xcorr_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                    C.c_double, vp, vp]
     L.rt_eval_medium.argtypes = [C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp, vp]
+    L.rt_validate_desc.argtypes = [C.POINTER(SceneDesc)]
+    L.rt_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(vp)]
+    L.rt_server_destroy.argtypes = [vp]
+    L.rt_server_destroy.restype = None
+    L.rt_submit.argtypes = [vp, C.POINTER(SceneDesc), vp, C.POINTER(C.c_uint64)]
+    L.rt_poll.argtypes = [vp, C.c_uint64, C.c_int32, C.POINTER(Result)]
+    L.rt_server_stats.argtypes = [vp, C.POINTER(ServerInfo)]
     L.rt_last_error.restype = C.c_char_p
     L.rt_version.restype = C.c_char_p
     _lib = L
@@ -313,3 +330,49 @@ def eval_medium(precision: int, Lambda: float, A: float, xy, out=None, stream=No
 
 def version() -> str:
     return lib().rt_version().decode()
+
+
+def validate(params: dict, tex: np.ndarray | None = None) -> None:
+    """rt_validate_desc: raise RtError for an invalid scene descriptor (host only)."""
+    desc, _keep = make_desc(params, tex)
+    _check(lib().rt_validate_desc(C.byref(desc)))
+
+
+class Server:
+    """Render server with continuous batching (rt_server_*, rt_submit, rt_poll)."""
+
+    def __init__(self, budget_bytes: int, max_inflight: int = 2):
+        h = C.c_void_p()
+        _check(lib().rt_server_create(int(budget_bytes), int(max_inflight), C.byref(h)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            lib().rt_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, params: dict, out, tex: np.ndarray | None = None) -> int:
+        desc, _keep = make_desc(params, tex)
+        t = C.c_uint64()
+        _check(lib().rt_submit(self._h, C.byref(desc), _ptr(out), C.byref(t)))
+        return t.value
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """The result dict when done; None while pending."""
+        r = Result()
+        rc = lib().rt_poll(self._h, ticket, int(timeout_us), C.byref(r))
+        if rc in (RT_PENDING, RT_ETIMEDOUT):
+            return None
+        _check(rc)
+        return {"status": r.status, "latency_ms": r.latency_ms, "queue_ms": r.queue_ms, "rays": r.rays}
+
+    def stats(self) -> dict:
+        i = ServerInfo()
+        _check(lib().rt_server_stats(self._h, C.byref(i)))
+        return {k: getattr(i, k) for k, _ in ServerInfo._fields_}

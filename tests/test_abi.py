@@ -79,3 +79,10 @@ def test_struct_layouts_match_header(rt, tmp_path):
         assert got[(cname, "size")] == C.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert got[(cname, f)] == getattr(cls, f).offset, (cname, f)
+
+
+def test_validate_desc_on_host(rt):
+    rt.validate(inputs.base_scene())
+    with pytest.raises(rt.RtError) as e:
+        rt.validate(inputs.base_scene(spp=0))
+    assert e.value.code == rt.RT_EINVAL

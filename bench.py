@@ -36,10 +36,16 @@ WORKLOAD = "grating cloak 512x512 4spp RK4 h=L/200, mirror+bare+cloak + centre l
 # Algorithmic FP32 operations (FMA = 2) per unit of work of the render kernel;
 # the counters of one launch give the units (see the kernel's w0_solve,
 # ray_force, w0_predict and rk4_step).
-FLOP_PER_NEWTON = 30
-FLOP_PER_EVAL = 47
-FLOP_PER_STEP = 81
+FLOP_PER_NEWTON = 33     # one Newton step on W + kA exp(-(W - ikz)) = 0 (rcp, ex2, sin, cos on MUFU)
+FLOP_PER_EVAL = 53       # continuation of W0, update of 1/(1+W0), force k n^2 (Im, Re) W r^2
+FLOP_PER_STEP = 105      # RK4 stage points, increments, compensated sums, event functions
 MUFU_PER_NEWTON = 4
+# DRAM bytes (read + write) of one cloaked-grating render launch of this
+# workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture
+# (--set full, one launch) of the current render kernel.  The image writes
+# stay in L2, so nearly nothing reaches DRAM.  Set to None when the kernel
+# changes.
+TRAFFIC_CLOAK_BYTES = 141056
 
 
 def peaks():
@@ -235,7 +241,7 @@ def run_gpu(args):
     mufu = MUFU_PER_NEWTON * cst["newton"]
     mufu_peak = 152 * 16 * clock_mhz * 1e6
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
-                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": None,
+                "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": TRAFFIC_CLOAK_BYTES,
                 "kernel": "render_kernel<float> (cloaked grating)",
                 "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max clock of {pk_kind} peaks file)",
                 "mufu_frac": round(mufu / (cl_ms * 1e-3) / mufu_peak, 4),
@@ -284,6 +290,9 @@ def run_gpu(args):
     d2h = sum(h.numel() * 4 for h in host.values()) + hc.numel() * 8 + hl.numel() * 8
     h2d = len(step.scenes) * 512      # scene parameters travel with each launch (DevScene by value)
 
+    batch = None if args.no_batch else bench_batch(rt, torch, stream)
+    serving = None if args.no_serving else bench_serving(rt, torch)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         cpu = cpu_baseline(args.cpu_seconds)
@@ -306,6 +315,8 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": {"value": round(rays_per_step / e2e_s / 1e6, 3), "unit": "Mrays/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "batched_64_scenes": batch,
+        "serving": serving,
         "gpu_launches": step.launches * args.steps,
         "clocks": clk,
         "wall_s_timed": round(t_wall, 3),
@@ -314,6 +325,68 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_batch(rt, torch, stream) -> dict:
+    """64 scenes drawn from seed 4 (sides 128..1024, spp 1/4/16, A, Lambda,
+    elevation and azimuth random) in one persistent launch replayed from a
+    CUDA graph, after the autotuner picked min_active."""
+    params = inputs.batch_scenes(count=64, seed=4, precision=inputs.FP32)
+    scenes = [rt.Scene(p) for p in params]
+    outs = [torch.zeros(sc.shape, dtype=torch.float32, device="cuda") for sc in scenes]
+    b = rt.Batch(scenes)
+    t0 = time.perf_counter()
+    m = b.autotune(outs, trials=1, stream=stream)
+    tune_s = time.perf_counter() - t0
+    b.render(outs, stream=stream)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        b.render(outs, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    st = b.stats()
+    b.close()
+    return {"scenes": 64, "rays": st["rays"], "ms": round(ms, 3), "Mrays_per_s": round(st["rays"] / ms / 1e3, 3),
+            "Gsteps_per_s": round(st["steps"] / ms / 1e6, 3), "min_active": m, "autotune_s": round(tune_s, 2)}
+
+
+def bench_serving(rt, torch) -> dict:
+    """Poisson arrivals of render requests (seed 5; side log-uniform in
+    [256, 2048], spp log-uniform in [1, 64]; scenes as in the batch workload)
+    served under a 40 GB ray-state budget: once at the offered 200 requests/s
+    (far above capacity: the queue builds, latency is the saturation value),
+    once at a rate the GPU sustains.  Latency is submission to completion."""
+    out = {}
+    for label, rate, count in (("offered_200_per_s", 200.0, 24), ("sustained", 2.0, 16)):
+        reqs = inputs.serving_requests(count, seed=5, rate=rate, precision=inputs.FP32)
+        imgs = [torch.zeros((p["height"], p["width"], 3), dtype=torch.float32, device="cuda") for _, p in reqs]
+        server = rt.Server(budget_bytes=40 * 10**9, max_inflight=4)
+        tickets = []
+        t0 = time.perf_counter()
+        for (t_arr, p), img in zip(reqs, imgs):
+            while time.perf_counter() - t0 < t_arr:
+                time.sleep(0.0002)
+            tickets.append(server.submit(p, img))
+        res = {}
+        while len(res) < len(tickets) and time.perf_counter() - t0 < 600:
+            for t in tickets:
+                if t not in res:
+                    r = server.poll(t, timeout_us=1000)
+                    if r is not None:
+                        res[t] = r
+        wall = time.perf_counter() - t0
+        server.close()
+        lat = np.array([r["latency_ms"] for r in res.values()])
+        rays = sum(r["rays"] for r in res.values())
+        out[label] = {"requests": len(reqs), "completed": len(res), "arrival_rate_per_s": rate,
+                      "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
+                      "Mrays_per_s": round(rays / wall / 1e6, 3), "wall_s": round(wall, 2)}
+        del imgs
+        torch.cuda.empty_cache()
+    return out
 
 
 def cpu_baseline(seconds: float) -> dict:
@@ -387,6 +460,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -167,14 +167,34 @@ def flush_l2(torch, buf):
     buf.add_(1)
 
 
+def rank_env() -> tuple[int, int, int]:
+    """(world size, rank, local rank) from the torchrun environment; (1, 0, 0) without it."""
+    return (int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("RANK", "0")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """Largest value of x over the ranks of the default process group."""
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job(rays_per_rank: int, world: int, total_ms: float, steps: int) -> tuple[float, float]:
+    """(ms per step, whole-job Mrays/s): every rank renders the same workload
+    (independent replicas), so the job processes world x rays_per_rank rays per
+    step in the slowest rank's time."""
+    ms_per_step = total_ms / steps
+    return ms_per_step, rays_per_rank * world / (ms_per_step * 1e-3) / 1e6
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
 
     from paper_1012_5107_gb300 import build as B
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    world, rank, local = rank_env()
     if world > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl")
@@ -221,12 +241,9 @@ def run_gpu(args):
     cloak_ms = np.array([a.elapsed_time(b) for a, b in evc])
     total_ms = float(step_ms.sum())
     if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    ms_per_step = total_ms / args.steps
+        total_ms = max_over_ranks(dist, total_ms, "cuda")
+    ms_per_step, value = whole_job(step.rays, world, total_ms, args.steps)
     rays_per_step = step.rays * world
-    value = rays_per_step / (ms_per_step * 1e-3) / 1e6
     steps_per_s = stats["steps"] * world / (ms_per_step * 1e-3)
     cvals = step.cvalues()
 
@@ -416,15 +433,14 @@ def cpu_baseline(seconds: float) -> dict:
 
 
 def run_reference(args):
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
+    world, rank, _ = rank_env()
     if world > 1 and rank != 0:
         return
     from oracle import oracle as orc
     orc.build()
     p = inputs.three_renders(inputs.config_main(precision=inputs.FP64))
     cores = orc.max_threads()
-    npix = 96   # per render per step: a bounded sample of the workload
+    npix = args.ref_pixels   # per render per step: a bounded sample of the workload
     scenes = {k: orc.Scene(v) for k, v in p.items()}
     for _ in range(args.warmup):
         for k, sc in scenes.items():
@@ -458,6 +474,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gratingrt", choices=["gratingrt", "reference"])
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--ref-pixels", type=int, default=96, help="pixels per render per step of the reference arm")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")

@@ -45,7 +45,7 @@ MUFU_PER_NEWTON = 4
 # (--set full, one launch) of the current render kernel.  The image writes
 # stay in L2, so nearly nothing reaches DRAM.  Set to None when the kernel
 # changes.
-TRAFFIC_CLOAK_BYTES = 141056
+TRAFFIC_CLOAK_BYTES = None
 
 
 def peaks():
@@ -259,7 +259,7 @@ def run_gpu(args):
     mufu_peak = 152 * 16 * clock_mhz * 1e6
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": TRAFFIC_CLOAK_BYTES,
-                "kernel": "render_kernel<float> (cloaked grating)",
+                "kernel": "wave_kernel<float, RK4> (cloaked grating)",
                 "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max clock of {pk_kind} peaks file)",
                 "mufu_frac": round(mufu / (cl_ms * 1e-3) / mufu_peak, 4),
                 "kernel_ms": round(cl_ms, 3)}

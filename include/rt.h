@@ -136,7 +136,12 @@ typedef struct rt_stats {
     uint64_t profile[4];      /* zero unless built with RT_PROFILE: per-warp
                                  cycles in the service pass and in the
                                  integration loop, loop iterations, and lanes
-                                 inside the cloak summed over the iterations    */
+                                 inside the cloak summed over the iterations
+                                 (wavefront variant: integration tasks, rays
+                                 they took, service tasks, rays they took)     */
+    uint64_t sched_timeouts;  /* wavefront variant: bounded waits on its work
+                                 queues that gave up (the image is then
+                                 incomplete and rt_scene_stats fails)           */
 } rt_stats;
 
 typedef struct rt_scene rt_scene;
@@ -177,17 +182,23 @@ int rt_render_pixels(rt_scene* scene, const int64_t* d_pix, int64_t npix, float*
  */
 int rt_render_host(rt_scene* scene, float* h_rgb, uint8_t* h_rgb8, void* stream);
 
-/* rt_scene_stats: counters of the last render of this scene (waits for it). */
+/* rt_scene_stats: counters of the last render of this scene (waits for it).
+   Returns RT_ETIMEDOUT (counters filled in) if that render gave up a bounded
+   wait of the wavefront loop's work queues. */
 int rt_scene_stats(rt_scene* scene, rt_stats* out);
 
 /*
  * rt_scene_set_launch: launch configuration of the scene's render kernel (the
  * knobs of the autotuner; results are identical for every setting).
- *   variant     compiled register budget: 0, 1, 2 = sized for 4, 5, 6
- *               resident blocks of 128 threads per SM; -1 keeps the current one
+ *   variant     0, 1, 2: the per-lane loop (one pixel per lane) compiled for
+ *               4, 5, 6 resident blocks of 128 threads per SM (1 and 2 for
+ *               FP32 RK4 only); 3: the wavefront loop (a pool of pixels in
+ *               flight per block, rays inside the cloak regrouped into full
+ *               warps); -1 keeps the current one
  *   min_active  the integration loop of a warp continues while at least this
  *               many of its 32 lanes are inside the cloak (1..32); 0 keeps it
- * Returns RT_EINVAL for values out of range.
+ * Returns RT_EINVAL for values out of range or a variant not compiled for the
+ * scene's precision and integrator.
  */
 int rt_scene_set_launch(rt_scene* scene, int32_t variant, int32_t min_active);
 
@@ -249,7 +260,9 @@ int rt_validate_desc(const rt_scene_desc* desc);
 /*
  * Serving: rt_submit queues a render request; a worker thread admits queued
  * requests in arrival order while the sum of their ray-state footprints
- * (64 bytes per sample plus the float output image) stays within the budget,
+ * (76 bytes per sample: 64 of ray state and a 12-byte colour slot; 16 bytes
+ * per pixel: the float output image and a sample counter; see
+ * rt_request_bytes) stays within the budget,
  * groups the newly admitted requests that share precision and integrator
  * into one batch launch and runs it on a free stream (at most max_inflight
  * batches in flight).  Requests that arrive while batches run are admitted as
@@ -270,6 +283,11 @@ typedef struct rt_server_info {
     uint64_t queued, in_flight, completed, failed;
     uint64_t bytes_in_use, budget;
 } rt_server_info;
+
+/* rt_request_bytes: the ray-state footprint a request of `desc` holds in a
+   server's budget while it is in flight (host only).  RT_EINVAL for an
+   invalid descriptor. */
+int rt_request_bytes(const rt_scene_desc* desc, uint64_t* bytes);
 
 /* rt_server_create: server on the current device; max_inflight 1..16. */
 int rt_server_create(size_t ray_state_budget_bytes, int32_t max_inflight, rt_server** out);

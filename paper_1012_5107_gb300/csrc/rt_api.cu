@@ -47,13 +47,16 @@ struct rt_scene {
     DevScene dev;
     int device;
     int nsm;
-    int variant;              // compiled register budget of the render kernel
+    int variant;              // launch variant of the render (per-lane loop or wavefront loop)
     int min_active;           // lanes inside the cloak that keep the integration loop going
     int grid;
     float* d_tex;
     unsigned long long* d_counters;
     float* d_host_rgb;        // buffers of rt_render_host
     uint8_t* d_host_rgb8;
+    float* d_samp;            // wavefront loop: per-sample colours and per-pixel counters,
+    int* d_pcnt;              // grown on demand (stream-ordered)
+    int64_t samp_cap, pix_cap;
     cudaEvent_t done;
     bool rendered;
 };
@@ -207,6 +210,7 @@ void counters_to_stats(const unsigned long long* c, rt_stats* out)
     out->fp64_refine = c[6];
     for (int q = 0; q < 5; ++q) out->status[q] = c[7 + q];
     for (int q = 0; q < 4; ++q) out->profile[q] = c[12 + q];
+    out->sched_timeouts = c[16];
 }
 
 }  // namespace grt
@@ -273,6 +277,8 @@ void rt_destroy_scene(rt_scene* s)
     if (s->d_counters) cudaFree(s->d_counters);
     if (s->d_host_rgb) cudaFree(s->d_host_rgb);
     if (s->d_host_rgb8) cudaFree(s->d_host_rgb8);
+    if (s->d_samp) cudaFree(s->d_samp);
+    if (s->d_pcnt) cudaFree(s->d_pcnt);
     if (s->done) cudaEventDestroy(s->done);
     free(s);
 }
@@ -291,9 +297,29 @@ static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float
     sc.pix_list = d_pix;
     sc.nwork = nwork;
     RT_CK(cudaMemsetAsync(s->d_counters, 0, kCounters * sizeof(unsigned long long), st));
+    SampleScratch ss = {nullptr, nullptr};
+    if (nwork > 0 && s->variant == kVariantWave && sc.spp > 1) {
+        // the wavefront loop traces the samples of a pixel at the same time
+        const int64_t ns = nwork * sc.spp;
+        if (ns > s->samp_cap || nwork > s->pix_cap) {
+            RT_CK(cudaStreamWaitEvent(st, s->done, 0));      // the last render of this scene is done with them
+            if (s->d_samp) RT_CK(cudaFreeAsync(s->d_samp, st));
+            if (s->d_pcnt) RT_CK(cudaFreeAsync(s->d_pcnt, st));
+            s->d_samp = nullptr;
+            s->d_pcnt = nullptr;
+            s->samp_cap = s->pix_cap = 0;
+            RT_CK(cudaMallocAsync((void**)&s->d_samp, (size_t)ns * kScratchBytesPerSample, st));
+            RT_CK(cudaMallocAsync((void**)&s->d_pcnt, (size_t)nwork * kScratchBytesPerPixel, st));
+            s->samp_cap = ns;
+            s->pix_cap = nwork;
+        }
+        RT_CK(cudaMemsetAsync(s->d_pcnt, 0, (size_t)nwork * kScratchBytesPerPixel, st));
+        ss.col = s->d_samp;
+        ss.cnt = s->d_pcnt;
+    }
     if (nwork > 0)
         RT_CK(launch_render(sc, s->desc.precision, s->variant, s->min_active, d_rgb, d_rgb8, d_rec, s->d_counters,
-                            s->grid, st));
+                            s->grid, ss, st));
     RT_CK(cudaEventRecord(s->done, st));
     s->rendered = true;
     return RT_OK;
@@ -340,6 +366,11 @@ int rt_scene_stats(rt_scene* s, rt_stats* out)
     RT_CK(cudaEventSynchronize(s->done));
     RT_CK(cudaMemcpy(c, s->d_counters, sizeof c, cudaMemcpyDeviceToHost));
     counters_to_stats(c, out);
+    if (out->sched_timeouts) {
+        set_error("the last render of this scene gave up %llu bounded waits of its work queues; its image is "
+                  "incomplete", (unsigned long long)out->sched_timeouts);
+        return RT_ETIMEDOUT;
+    }
     return RT_OK;
 }
 
@@ -358,7 +389,6 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
              (int)floor(log2(samples > 1.0 ? samples : 1.0)));
     int v = kDefaultVariant, m = kMinActive;
     if (!tune_lookup(key, &v, &m)) {
-        const int nvar = (d.precision == RT_FP32 && d.integrator == RT_RK4) ? kVariants : 1;
         const int cand[] = {12, 16, 20, 24, 28};
         cudaStream_t st = (cudaStream_t)stream;
         cudaEvent_t e0, e1;
@@ -366,7 +396,8 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
         RT_CK(cudaEventCreate(&e1));
         float best = 1e30f;
         int rc = RT_OK;
-        for (int var = 0; var < nvar && rc == RT_OK; ++var) {
+        for (int var = 0; var < kVariants && rc == RT_OK; ++var) {
+            if (!variant_compiled(d.precision, d.integrator, var)) continue;
             for (int c : cand) {
                 rc = rt_scene_set_launch(s, var, c);
                 if (rc != RT_OK) break;
@@ -401,6 +432,8 @@ int rt_scene_set_launch(rt_scene* s, int32_t variant, int32_t min_active)
     g_err[0] = 0;
     RT_REQ(s, "scene is NULL");
     RT_REQ(variant >= -1 && variant < kVariants, "variant must be -1 (keep) or 0..%d", kVariants - 1);
+    RT_REQ(variant < 0 || variant_compiled(s->desc.precision, s->desc.integrator, variant),
+           "variant %d is not compiled for this precision and integrator", variant);
     RT_REQ(min_active == 0 || (min_active >= 1 && min_active <= 32), "min_active must be 0 (keep) or 1..32");
     if (variant >= 0 && variant != s->variant) {
         int bps = 0;

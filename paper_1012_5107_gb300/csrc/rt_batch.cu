@@ -9,15 +9,37 @@
 #include <string>
 #include <vector>
 
+#include <atomic>
+
 #include "rt_internal.h"
-#include "rt_trace.cuh"
+#include "rt_wave.cuh"
 
 namespace grt {
+
+// Many scenes in one launch of the wavefront loop: their samples form one
+// work list, so the warps balance across scenes of uneven size.
+template <class R, int INTEG>
+static cudaError_t batch_prepare()
+{
+    static std::atomic<unsigned long long> done{0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(wave_batch_kernel<R, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)wave_smem_bytes<R>());
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
 
 template <class R, int INTEG>
 static cudaError_t batch_occupancy_t(int* bps)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_batch_kernel<R, INTEG>, kRenderBlock, 0);
+    const cudaError_t e = batch_prepare<R, INTEG>();
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_batch_kernel<R, INTEG>, kWaveBlock,
+                                                         wave_smem_bytes<R>());
 }
 
 cudaError_t batch_occupancy(int precision, int integrator, int* bps)
@@ -27,26 +49,22 @@ cudaError_t batch_occupancy(int precision, int integrator, int* bps)
     return integrator == RT_DP45 ? batch_occupancy_t<float, RT_DP45>(bps) : batch_occupancy_t<float, RT_RK4>(bps);
 }
 
-cudaError_t launch_batch(int precision, int integrator, const DevScene* scenes, const int64_t* offsets,
-                         float* const* rgbs, int n, int64_t total, unsigned long long* counters, int min_active,
-                         int grid, cudaStream_t stream)
+template <class R, int INTEG>
+static cudaError_t launch_batch_t(const BatchLaunch& L, cudaStream_t stream)
 {
-    if (precision == RT_FP64) {
-        if (integrator == RT_DP45)
-            render_batch_kernel<double, RT_DP45><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
-                                                                                   counters, min_active);
-        else
-            render_batch_kernel<double, RT_RK4><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
-                                                                                  counters, min_active);
-    } else {
-        if (integrator == RT_DP45)
-            render_batch_kernel<float, RT_DP45><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
-                                                                                  counters, min_active);
-        else
-            render_batch_kernel<float, RT_RK4><<<grid, kRenderBlock, 0, stream>>>(scenes, offsets, rgbs, n, total,
-                                                                                 counters, min_active);
-    }
+    const cudaError_t e = batch_prepare<R, INTEG>();
+    if (e != cudaSuccess) return e;
+    wave_batch_kernel<R, INTEG><<<L.grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+        L.scenes, L.offsets, L.soffsets, L.rgbs, L.n, L.total, L.total_samples, L.scratch.col, L.scratch.cnt,
+        L.counters, L.min_active);
     return cudaGetLastError();
+}
+
+cudaError_t launch_batch(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream)
+{
+    if (precision == RT_FP64)
+        return integrator == RT_DP45 ? launch_batch_t<double, RT_DP45>(L, stream) : launch_batch_t<double, RT_RK4>(L, stream);
+    return integrator == RT_DP45 ? launch_batch_t<float, RT_DP45>(L, stream) : launch_batch_t<float, RT_RK4>(L, stream);
 }
 
 // ------------------------------------------------------------------------
@@ -124,9 +142,12 @@ using namespace grt;
 
 struct rt_batch {
     int n, device, precision, integrator, grid, nsm, min_active;
-    int64_t total;
+    int64_t total, total_samples;
     DevScene* d_scenes;
-    int64_t* d_offsets;
+    int64_t* d_offsets;      // first pixel of each scene
+    int64_t* d_soffsets;     // first sample of each scene
+    float* d_samp;           // per-sample colours of multi-sample pixels
+    int* d_pcnt;             // per-pixel sample counters
     float** d_rgbs;
     std::vector<float*> h_rgbs;        // output pointers last uploaded
     unsigned long long* d_counters;
@@ -144,7 +165,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     *out = nullptr;
     RT_REQ(scenes && n >= 1, "need at least one scene");
     std::vector<DevScene> dev(n);
-    std::vector<int64_t> off(n + 1, 0);
+    std::vector<int64_t> off(n + 1, 0), soff(n + 1, 0);
     int precision = -1, integrator = -1, device = -1;
     for (int i = 0; i < n; ++i) {
         RT_REQ(scenes[i], "scene %d is NULL", i);
@@ -155,6 +176,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
         RT_REQ(p == precision && g == integrator, "scenes of a batch must share precision and integrator (scene %d)", i);
         RT_REQ(d == device, "scenes of a batch must live on one device (scene %d)", i);
         off[i + 1] = off[i] + dev[i].nwork;
+        soff[i + 1] = soff[i] + dev[i].nwork * dev[i].spp;
     }
     int cur = -1;
     RT_CK(cudaGetDevice(&cur));
@@ -166,15 +188,20 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     b->precision = precision;
     b->integrator = integrator;
     b->total = off[n];
+    b->total_samples = soff[n];
     b->min_active = kMinActive;
     b->graph_min_active = -1;
     b->h_rgbs.assign(n, nullptr);
     cudaError_t e = cudaMalloc(&b->d_scenes, sizeof(DevScene) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_offsets, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_soffsets, sizeof(int64_t) * (n + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_samp, kScratchBytesPerSample * (size_t)b->total_samples);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_pcnt, kScratchBytesPerPixel * (size_t)b->total);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_rgbs, sizeof(float*) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned long long) * kCounters);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_scenes, dev.data(), sizeof(DevScene) * n, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(b->d_offsets, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_soffsets, soff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemset(b->d_rgbs, 0, sizeof(float*) * n);
     if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned long long) * kCounters);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
@@ -199,6 +226,9 @@ void rt_batch_destroy(rt_batch* b)
     if (b->graph) cudaGraphDestroy(b->graph);
     if (b->d_scenes) cudaFree(b->d_scenes);
     if (b->d_offsets) cudaFree(b->d_offsets);
+    if (b->d_soffsets) cudaFree(b->d_soffsets);
+    if (b->d_samp) cudaFree(b->d_samp);
+    if (b->d_pcnt) cudaFree(b->d_pcnt);
     if (b->d_rgbs) cudaFree(b->d_rgbs);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->done) cudaEventDestroy(b->done);
@@ -226,9 +256,10 @@ int rt_batch_render(rt_batch* b, float* const* d_rgb, void* stream)
         RT_CK(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
         cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * kCounters, cap);
-        if (e == cudaSuccess)
-            e = launch_batch(b->precision, b->integrator, b->d_scenes, b->d_offsets, b->d_rgbs, b->n, b->total,
-                             b->d_counters, b->min_active, b->grid, cap);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->d_pcnt, 0, kScratchBytesPerPixel * (size_t)b->total, cap);
+        const BatchLaunch L = {b->d_scenes, b->d_offsets, b->d_soffsets, b->d_rgbs, b->n, b->total,
+                               b->total_samples, {b->d_samp, b->d_pcnt}, b->d_counters, b->min_active, b->grid};
+        if (e == cudaSuccess) e = launch_batch(b->precision, b->integrator, L, cap);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &g);
         cudaStreamDestroy(cap);
@@ -250,6 +281,11 @@ int rt_batch_stats(rt_batch* b, rt_stats* out)
     RT_CK(cudaEventSynchronize(b->done));
     RT_CK(cudaMemcpy(c, b->d_counters, sizeof c, cudaMemcpyDeviceToHost));
     counters_to_stats(c, out);
+    if (out->sched_timeouts) {
+        set_error("the last render of this batch gave up %llu bounded waits of its work queues; its images are "
+                  "incomplete", (unsigned long long)out->sched_timeouts);
+        return RT_ETIMEDOUT;
+    }
     return RT_OK;
 }
 

@@ -9,14 +9,18 @@
 namespace grt {
 
 constexpr int kRenderBlock = 128;
-// Compiled register budgets of the render kernel: resident blocks of
-// kRenderBlock threads per SM that each variant is sized for.
-constexpr int kVariants = 3;
-constexpr int kVariantBlocks[kVariants] = {4, 5, 6};
-constexpr int kDefaultVariant = 0;
-constexpr int kMinActive = 24;   // step while at least this many lanes of a warp are inside the cloak
+// Launch variants of the render: 0..2 are the per-lane loop (rt_trace.cuh)
+// compiled for 4, 5 and 6 resident blocks of kRenderBlock threads per SM;
+// kVariantWave is the wavefront loop (rt_wave.cuh).
+constexpr int kVariants = 4;
+constexpr int kLaneVariants = 3;
+constexpr int kVariantBlocks[kLaneVariants] = {4, 5, 6};
+constexpr int kVariantWave = 3;
+constexpr int kDefaultVariant = kVariantWave;
+constexpr int kMinActive = 28;   // an integration task continues while at least this many of its 32 rays are inside the cloak
 constexpr int kMaxWindows = 16;
-constexpr int kCounters = 16;      // [0] work counter, [1..11] statistics, [12..15] optional profile
+constexpr int kCounters = 17;      // [0] work counter, [1..11] statistics, [12..15] optional profile,
+                                   // [16] wavefront-loop waits that timed out
 
 #ifndef RT_PROFILE
 #define RT_PROFILE 0
@@ -27,9 +31,21 @@ struct Windows {
     int j0[kMaxWindows], j1[kMaxWindows];
 };
 
+// Whether launch variant `variant` exists for this precision and integrator.
+bool variant_compiled(int precision, int integrator, int variant);
 cudaError_t render_occupancy(int precision, int integrator, int variant, int* blocks_per_sm);
+// Scratch of the wavefront loop for pixels of several samples: 3 floats per
+// sample (col) and one counter per pixel (cnt, zero at launch).
+struct SampleScratch {
+    float* col;
+    int* cnt;
+};
+constexpr size_t kScratchBytesPerSample = 3 * sizeof(float);
+constexpr size_t kScratchBytesPerPixel = sizeof(int);
+
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
-                          rt_ray_record* rec, unsigned long long* counters, int grid, cudaStream_t stream);
+                          rt_ray_record* rec, unsigned long long* counters, int grid, const SampleScratch& ss,
+                          cudaStream_t stream);
 cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,
                           cudaStream_t stream);
 
@@ -62,9 +78,19 @@ bool tune_lookup(const std::string& key, int* variant, int* min_active);
 // Scene table of a validated descriptor (texture pointer left to the caller).
 void build_scene_table(const rt_scene_desc* d, DevScene* s);
 cudaError_t batch_occupancy(int precision, int integrator, int* bps);
-cudaError_t launch_batch(int precision, int integrator, const DevScene* scenes, const int64_t* offsets,
-                         float* const* rgbs, int n, int64_t total, unsigned long long* counters, int min_active,
-                         int grid, cudaStream_t stream);
+// One launch of the wavefront loop over the pixels of n scenes (device tables).
+struct BatchLaunch {
+    const DevScene* scenes;
+    const int64_t* offsets;      // n + 1: first pixel of each scene
+    const int64_t* soffsets;     // n + 1: first sample of each scene
+    float* const* rgbs;          // n output images
+    int n;
+    int64_t total, total_samples;
+    SampleScratch scratch;       // for total_samples samples and total pixels
+    unsigned long long* counters;
+    int min_active, grid;
+};
+cudaError_t launch_batch(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream);
 void tune_record(const std::string& key, int variant, int min_active);
 
 }  // namespace grt

@@ -1,14 +1,45 @@
 // rt_render.cu -- instantiations and launchers of the render and medium
-// kernels (the kernels themselves are in rt_trace.cuh).
-#include "rt_trace.cuh"
+// kernels (the kernels themselves are in rt_trace.cuh and rt_wave.cuh).
+#include <atomic>
+
+#include "rt_wave.cuh"
 
 namespace grt {
 
-// Register-budget variants are compiled for the FP32 RK4 kernel, the one the
-// benchmark times; the other (precision, integrator) pairs have one each.
+// The wavefront kernels keep their pixel pool in dynamic shared memory above
+// the default 48 KB; the limit is raised once per kernel and device.
+template <class K>
+static cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<unsigned long long>& done)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = 1ull << (dev & 63);
+    if (done.load() & bit) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done.fetch_or(bit);
+    return e;
+}
+
+template <class R, int INTEG>
+static cudaError_t wave_prepare()
+{
+    static std::atomic<unsigned long long> done{0};
+    return allow_smem(wave_kernel<R, INTEG>, wave_smem_bytes<R>(), done);
+}
+
+// Register-budget variants of the per-lane loop are compiled for the FP32 RK4
+// kernel, the one the benchmark times; the other (precision, integrator)
+// pairs have one each.  Every pair has the wavefront loop.
 template <class R, int INTEG>
 static cudaError_t occupancy_t(int variant, int* bps)
 {
+    if (variant == kVariantWave) {
+        const cudaError_t e = wave_prepare<R, INTEG>();
+        if (e != cudaSuccess) return e;
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG>, kWaveBlock,
+                                                             wave_smem_bytes<R>());
+    }
     if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
         if (variant == 1)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[1], INTEG>, kRenderBlock, 0);
@@ -19,20 +50,35 @@ static cudaError_t occupancy_t(int variant, int* bps)
 }
 
 template <class R, int INTEG>
-static void launch_t(const DevScene& sc, int variant, int min_active, float* rgb, uint8_t* rgb8, rt_ray_record* rec,
-                     unsigned long long* counters, int grid, cudaStream_t stream)
+static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, float* rgb, uint8_t* rgb8,
+                            rt_ray_record* rec, unsigned long long* counters, int grid, const SampleScratch& ss,
+                            cudaStream_t stream)
 {
+    if (variant == kVariantWave) {
+        const cudaError_t e = wave_prepare<R, INTEG>();
+        if (e != cudaSuccess) return e;
+        wave_kernel<R, INTEG><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(sc, rgb, rgb8, rec, counters,
+                                                                                  min_active, ss.col, ss.cnt);
+        return cudaGetLastError();
+    }
     if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
         if (variant == 1) {
             render_kernel<R, kVariantBlocks[1], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
-            return;
+            return cudaGetLastError();
         }
         if (variant == 2) {
             render_kernel<R, kVariantBlocks[2], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
-            return;
+            return cudaGetLastError();
         }
     }
     render_kernel<R, kVariantBlocks[0], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
+    return cudaGetLastError();
+}
+
+bool variant_compiled(int precision, int integrator, int variant)
+{
+    if (variant == 0 || variant == kVariantWave) return true;
+    return precision == RT_FP32 && integrator == RT_RK4 && variant >= 0 && variant < kLaneVariants;
 }
 
 cudaError_t render_occupancy(int precision, int integrator, int variant, int* blocks_per_sm)
@@ -45,16 +91,17 @@ cudaError_t render_occupancy(int precision, int integrator, int variant, int* bl
 }
 
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
-                          rt_ray_record* rec, unsigned long long* counters, int grid, cudaStream_t stream)
+                          rt_ray_record* rec, unsigned long long* counters, int grid, const SampleScratch& ss,
+                          cudaStream_t stream)
 {
     if (precision == RT_FP64) {
-        if (sc.integrator == RT_DP45) launch_t<double, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
-        else launch_t<double, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
-    } else {
-        if (sc.integrator == RT_DP45) launch_t<float, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
-        else launch_t<float, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, stream);
+        if (sc.integrator == RT_DP45)
+            return launch_t<double, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
+        return launch_t<double, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
     }
-    return cudaGetLastError();
+    if (sc.integrator == RT_DP45)
+        return launch_t<float, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
+    return launch_t<float, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
 }
 
 cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,

@@ -28,7 +28,8 @@ using Clock = std::chrono::steady_clock;
 
 // Bytes of ray state a request holds while it is in flight: every sample of
 // the image carries its state through the batch (position, direction,
-// cloak state, accumulators), 64 bytes per sample, plus its output image.
+// cloak state, accumulators), 64 bytes per sample, plus its colour slot and
+// its pixel's sample counter in the launch's scratch and its output image.
 constexpr size_t kStateBytesPerSample = 64;
 
 struct Request {
@@ -77,7 +78,8 @@ static size_t request_bytes(const rt_scene_desc* d)
 {
     const size_t wout = d->centre_line ? 1 : (size_t)d->width;
     const size_t pixels = (size_t)d->height * wout;
-    return pixels * (size_t)d->spp * kStateBytesPerSample + pixels * 3 * sizeof(float);
+    return pixels * (size_t)d->spp * (kStateBytesPerSample + kScratchBytesPerSample) +
+           pixels * (3 * sizeof(float) + kScratchBytesPerPixel);
 }
 
 // Launch one batch of admitted requests on stream `si` (worker thread, lock
@@ -92,7 +94,7 @@ static void launch_flight(rt_server* S, const std::vector<uint64_t>& tickets, in
     f.d_counters = nullptr;
     const int n = (int)tickets.size();
     std::vector<DevScene> dev(n);
-    std::vector<int64_t> off(n + 1, 0);
+    std::vector<int64_t> off(n + 1, 0), soff(n + 1, 0);
     std::vector<float*> outs(n);
     cudaError_t e = cudaSuccess;
     auto alloc = [&](void** p, size_t bytes) {
@@ -110,21 +112,30 @@ static void launch_flight(rt_server* S, const std::vector<uint64_t>& tickets, in
             dev[i].tex = (const float*)t;
         }
         off[i + 1] = off[i] + dev[i].nwork;
+        soff[i + 1] = soff[i] + dev[i].nwork * dev[i].spp;
         outs[i] = r.d_out;
     }
-    void *d_scenes = nullptr, *d_off = nullptr, *d_rgbs = nullptr, *d_cnt = nullptr;
+    void *d_scenes = nullptr, *d_off = nullptr, *d_soff = nullptr, *d_rgbs = nullptr, *d_cnt = nullptr;
+    void *d_samp = nullptr, *d_pcnt = nullptr;
     alloc(&d_scenes, sizeof(DevScene) * n);
     alloc(&d_off, sizeof(int64_t) * (n + 1));
+    alloc(&d_soff, sizeof(int64_t) * (n + 1));
     alloc(&d_rgbs, sizeof(float*) * n);
     alloc(&d_cnt, sizeof(unsigned long long) * kCounters);
+    alloc(&d_samp, kScratchBytesPerSample * (size_t)soff[n]);
+    alloc(&d_pcnt, kScratchBytesPerPixel * (size_t)off[n]);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_scenes, dev.data(), sizeof(DevScene) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_off, off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(d_soff, soff.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(d_rgbs, outs.data(), sizeof(float*) * n, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = cudaMemsetAsync(d_cnt, 0, sizeof(unsigned long long) * kCounters, st);
-    if (e == cudaSuccess)
-        e = launch_batch(S->precision_of(tickets[0]), S->integrator_of(tickets[0]), (const DevScene*)d_scenes,
-                         (const int64_t*)d_off, (float* const*)d_rgbs, n, off[n], (unsigned long long*)d_cnt,
-                         kMinActive, S->grid, st);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d_pcnt, 0, kScratchBytesPerPixel * (size_t)off[n], st);
+    if (e == cudaSuccess) {
+        const BatchLaunch L = {(const DevScene*)d_scenes, (const int64_t*)d_off, (const int64_t*)d_soff,
+                               (float* const*)d_rgbs, n, off[n], soff[n], {(float*)d_samp, (int*)d_pcnt},
+                               (unsigned long long*)d_cnt, kMinActive, S->grid};
+        e = launch_batch(S->precision_of(tickets[0]), S->integrator_of(tickets[0]), L, st);
+    }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaEventRecord(f.done, st);
     // pageable-memory copies are staged before cudaMemcpyAsync returns, so the
@@ -157,7 +168,18 @@ static void retire(rt_server* S)
         Flight& f = S->flights[i];
         const cudaError_t q = cudaEventQuery(f.done);
         if (q == cudaErrorNotReady) { ++i; continue; }
-        const int status = (q == cudaSuccess) ? RT_OK : RT_ECUDA;
+        int status = (q == cudaSuccess) ? RT_OK : RT_ECUDA;
+        if (status == RT_OK) {
+            // a bounded wait of the work queues that gave up leaves images incomplete
+            unsigned long long timeouts = 0;
+            cudaStream_t st = S->streams[f.stream];
+            if (cudaMemcpyAsync(&timeouts, f.d_counters + (kCounters - 1), sizeof timeouts, cudaMemcpyDeviceToHost,
+                                st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess)
+                status = RT_ECUDA;
+            else if (timeouts)
+                status = RT_ETIMEDOUT;
+        }
         const Clock::time_point now = Clock::now();
         for (size_t k = 0; k < f.tickets.size(); ++k) {
             Request& r = S->req[f.tickets[k]];
@@ -222,6 +244,15 @@ static void worker_main(rt_server* S)
 }
 
 extern "C" {
+
+int rt_request_bytes(const rt_scene_desc* desc, uint64_t* bytes)
+{
+    if (!desc || !bytes) { set_error("desc and bytes must not be NULL"); return RT_EINVAL; }
+    const int rc = rt_validate_desc(desc);
+    if (rc != RT_OK) return rc;
+    *bytes = request_bytes(desc);
+    return RT_OK;
+}
 
 int rt_server_create(size_t ray_state_budget_bytes, int32_t max_inflight, rt_server** out)
 {

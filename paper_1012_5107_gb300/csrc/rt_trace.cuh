@@ -68,6 +68,7 @@ struct Cold {
     float acc[3], col[3];
     int sample, bounces, events, status;
     uint32_t rays, nevents, stat[5];
+    int phase, surf, steps;   // the wavefront loop (rt_wave.cuh): state of a pixel between tasks
 };
 
 // ------------------------------------------------------------------------
@@ -990,19 +991,35 @@ __device__ __forceinline__ uint8_t quantize8(float c)
 // Where the work of a launch comes from: one scene (constants in the kernel
 // parameters) or a table of scenes whose pixels are numbered one after the
 // other (constants in device memory).
+// Pixels are numbered by work item (w), samples by w * spp + sample; the
+// wavefront loop takes samples as its work items, the per-lane loop pixels.
+// Samples of one pixel traced by different lanes leave their colours in
+// samp_col (3 floats per sample) and count themselves in pix_cnt (one int per
+// pixel, zero at launch); the last one sums them in sample order.
 struct OneScene {
     const DevScene& sc;
     float* rgb;
     uint8_t* rgb8;
     rt_ray_record* rec;
+    float* samp_col;
+    int* pix_cnt;
     __device__ __forceinline__ const DevScene& scene(int) const { return sc; }
     __device__ __forceinline__ int64_t nwork() const { return sc.nwork; }
+    __device__ __forceinline__ int64_t nsamples() const { return sc.nwork * sc.spp; }
     __device__ __forceinline__ void map(int64_t w, int& s, int64_t& pix, int64_t& out) const
     {
         s = 0;
         out = w;
         pix = sc.pix_list ? sc.pix_list[w] : w;
     }
+    __device__ __forceinline__ void map_sample(int64_t ws, int& s, int64_t& pix, int64_t& out, int& sample) const
+    {
+        const int64_t w = ws / sc.spp;
+        sample = (int)(ws - w * sc.spp);
+        map(w, s, pix, out);
+    }
+    __device__ __forceinline__ int64_t sample_slot(int, int64_t out, int sample) const { return out * sc.spp + sample; }
+    __device__ __forceinline__ int64_t pixel_slot(int, int64_t out) const { return out; }
     __device__ __forceinline__ float* rgb_of(int) const { return rgb; }
     __device__ __forceinline__ uint8_t* rgb8_of(int) const { return rgb8; }
     __device__ __forceinline__ rt_ray_record* rec_of(int) const { return rec; }
@@ -1010,23 +1027,46 @@ struct OneScene {
 
 struct ManyScenes {
     const DevScene* scenes;
-    const int64_t* offsets;          // n + 1 entries: first work item of each scene
+    const int64_t* offsets;          // n + 1 entries: first pixel of each scene
+    const int64_t* soffsets;         // n + 1 entries: first sample of each scene
     float* const* rgbs;              // per-scene output images
     int n;
-    int64_t total;
+    int64_t total, total_samples;
+    float* samp_col;
+    int* pix_cnt;
     __device__ __forceinline__ const DevScene& scene(int s) const { return scenes[s]; }
     __device__ __forceinline__ int64_t nwork() const { return total; }
-    __device__ __forceinline__ void map(int64_t w, int& s, int64_t& pix, int64_t& out) const
+    __device__ __forceinline__ int64_t nsamples() const { return total_samples; }
+    // last scene whose first entry in `table` is <= w
+    __device__ __forceinline__ int find(const int64_t* table, int64_t w) const
     {
         int lo = 0, hi = n - 1;
-        while (lo < hi) {                 // last scene whose first item is <= w
+        while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
-            if (__ldg(offsets + mid) <= w) lo = mid;
+            if (__ldg(table + mid) <= w) lo = mid;
             else hi = mid - 1;
         }
-        s = lo;
-        out = pix = w - __ldg(offsets + lo);
+        return lo;
     }
+    __device__ __forceinline__ void map(int64_t w, int& s, int64_t& pix, int64_t& out) const
+    {
+        s = find(offsets, w);
+        out = pix = w - __ldg(offsets + s);
+    }
+    __device__ __forceinline__ void map_sample(int64_t ws, int& s, int64_t& pix, int64_t& out, int& sample) const
+    {
+        s = find(soffsets, ws);
+        const int64_t l = ws - __ldg(soffsets + s);
+        const int spp = scenes[s].spp;
+        const int64_t w = l / spp;
+        sample = (int)(l - w * spp);
+        out = pix = w;
+    }
+    __device__ __forceinline__ int64_t sample_slot(int s, int64_t out, int sample) const
+    {
+        return __ldg(soffsets + s) + out * scenes[s].spp + sample;
+    }
+    __device__ __forceinline__ int64_t pixel_slot(int s, int64_t out) const { return __ldg(offsets + s) + out; }
     __device__ __forceinline__ float* rgb_of(int s) const { return rgbs[s]; }
     __device__ __forceinline__ uint8_t* rgb8_of(int) const { return nullptr; }
     __device__ __forceinline__ rt_ray_record* rec_of(int) const { return nullptr; }
@@ -1139,18 +1179,7 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
                                                                     uint8_t* __restrict__ rgb8, rt_ray_record* rec,
                                                                     unsigned long long* counters, int min_active)
 {
-    const OneScene src{sc, rgb, rgb8, rec};
-    render_loop<R, INTEG>(src, counters, min_active);
-}
-
-// Many scenes in one launch (same precision and integrator): their pixels
-// form one work list, so the warps balance across scenes of uneven size.
-template <class R, int INTEG>
-__global__ void __launch_bounds__(kRenderBlock, kVariantBlocks[0]) render_batch_kernel(
-    const DevScene* __restrict__ scenes, const int64_t* __restrict__ offsets, float* const* __restrict__ rgbs, int n,
-    int64_t total, unsigned long long* counters, int min_active)
-{
-    const ManyScenes src{scenes, offsets, rgbs, n, total};
+    const OneScene src{sc, rgb, rgb8, rec, nullptr, nullptr};
     render_loop<R, INTEG>(src, counters, min_active);
 }
 

@@ -70,7 +70,7 @@ class ServerInfo(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("rays", C.c_uint64), ("steps", C.c_uint64), ("evals", C.c_uint64), ("newton", C.c_uint64),
                 ("events", C.c_uint64), ("fp64_refine", C.c_uint64), ("status", C.c_uint64 * 5),
-                ("profile", C.c_uint64 * 4)]
+                ("profile", C.c_uint64 * 4), ("sched_timeouts", C.c_uint64)]
 
 
 _lib = None
@@ -79,7 +79,8 @@ EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels
            "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_scene_autotune",
            "rt_batch_create", "rt_batch_destroy", "rt_batch_render", "rt_batch_stats", "rt_batch_set_launch",
            "rt_batch_get_launch", "rt_batch_autotune",
-           "rt_validate_desc", "rt_server_create", "rt_server_destroy", "rt_submit", "rt_poll", "rt_server_stats",
+           "rt_validate_desc", "rt_request_bytes", "rt_server_create", "rt_server_destroy", "rt_submit", "rt_poll",
+           "rt_server_stats",
            "rt_xcorr", "rt_xcorr_noalloc", "rt_eval_medium", "rt_last_error", "rt_version"]
 
 
@@ -117,6 +118,7 @@ def lib() -> C.CDLL:
                                    C.c_double, vp, vp]
     L.rt_eval_medium.argtypes = [C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp, vp]
     L.rt_validate_desc.argtypes = [C.POINTER(SceneDesc)]
+    L.rt_request_bytes.argtypes = [C.POINTER(SceneDesc), C.POINTER(C.c_uint64)]
     L.rt_server_create.argtypes = [C.c_size_t, C.c_int32, C.POINTER(vp)]
     L.rt_server_destroy.argtypes = [vp]
     L.rt_server_destroy.restype = None
@@ -230,7 +232,8 @@ class Scene:
 
 def _stats_dict(s: Stats) -> dict:
     return {"rays": s.rays, "steps": s.steps, "evals": s.evals, "newton": s.newton, "events": s.events,
-            "fp64_refine": s.fp64_refine, "status": list(s.status), "profile": list(s.profile)}
+            "fp64_refine": s.fp64_refine, "status": list(s.status), "profile": list(s.profile),
+            "sched_timeouts": s.sched_timeouts}
 
 
 class Batch:
@@ -336,6 +339,14 @@ def validate(params: dict, tex: np.ndarray | None = None) -> None:
     """rt_validate_desc: raise RtError for an invalid scene descriptor (host only)."""
     desc, _keep = make_desc(params, tex)
     _check(lib().rt_validate_desc(C.byref(desc)))
+
+
+def request_bytes(params: dict) -> int:
+    """Ray-state footprint of a request in a server's budget (rt_request_bytes)."""
+    desc, _keep = make_desc(params, None)
+    b = C.c_uint64()
+    _check(lib().rt_request_bytes(C.byref(desc), C.byref(b)))
+    return b.value
 
 
 class Server:

@@ -86,3 +86,19 @@ def test_validate_desc_on_host(rt):
     with pytest.raises(rt.RtError) as e:
         rt.validate(inputs.base_scene(spp=0))
     assert e.value.code == rt.RT_EINVAL
+
+
+@pytest.mark.parametrize("over", [dict(width=64, height=48, spp=4), dict(width=33, height=17, spp=1, centre_line=1),
+                                  dict(width=256, height=256, spp=64)])
+def test_request_bytes(rt, over):
+    """A request's footprint in a server budget: 76 bytes per sample (ray state
+    and a colour slot) and 16 per pixel (output colour and a sample counter)."""
+    p = inputs.base_scene(**over)
+    wout = 1 if p["centre_line"] else p["width"]
+    assert rt.request_bytes(p) == p["height"] * wout * (76 * p["spp"] + 16)
+
+
+def test_request_bytes_rejects_invalid(rt):
+    with pytest.raises(rt.RtError) as e:
+        rt.request_bytes(inputs.base_scene(width=0))
+    assert e.value.code == rt.RT_EINVAL

@@ -35,8 +35,10 @@ def torch():
     return t
 
 
-def gpu_render(rt, torch, p, records=True, tex=None):
+def gpu_render(rt, torch, p, records=True, tex=None, variant=None, min_active=0):
     sc = rt.Scene(p, tex=tex)
+    if variant is not None:
+        sc.set_launch(variant, min_active)
     rgb = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
     rgb8 = torch.zeros(sc.shape, dtype=torch.uint8, device="cuda")
     rec = torch.zeros(sc.height * sc.wout * sc.spp * 80, dtype=torch.uint8, device="cuda") if records else None
@@ -274,9 +276,10 @@ def test_render_is_deterministic(rt, torch):
     dict(width=12, height=12, spp=4, elev_deg=10.0, azim_deg=35.0, Lambda=0.6, A=0.03, E=4.8, H=1.2),
 ])
 @pytest.mark.parametrize("precision", [1, 0])
-def test_edge_cases(rt, torch, orc, over, precision):
+@pytest.mark.parametrize("variant", [0, 3])
+def test_edge_cases(rt, torch, orc, over, precision, variant):
     p = inputs.base_scene(**over, precision=precision)
-    g = gpu_render(rt, torch, p)
+    g = gpu_render(rt, torch, p, variant=variant)
     o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
     n = o_rec.size
     if precision == 1:
@@ -389,3 +392,81 @@ def test_hd_workload_sampled(rt, torch, orc, extent, A):
     cond = fp32_resolvable(orc, p, pix_np, 16, o_rec, tex)
     compare_records(g, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.97)
     assert np.median(np.abs(rgb.cpu().numpy() - o_rgb)) < 1e-4
+
+
+# ---------------------------------------------------------------------------
+# Launch variants: the per-lane loop and the wavefront loop trace every ray
+# with the same arithmetic; only the grouping of rays into warps differs.
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("precision,integrator", [(0, 0), (1, 0), (0, 1), (1, 1)])
+@pytest.mark.parametrize("kind", ["mirror", "bare", "cloak"])
+def test_wave_equals_lane_loop(rt, torch, precision, integrator, kind):
+    p = inputs.three_renders(inputs.base_scene(width=96, height=80, spp=4, seed=5, integrator=integrator,
+                                               rtol=1e-5 if precision == 0 else 1e-7,
+                                               atol=1e-5 if precision == 0 else 1e-7,
+                                               precision=precision))[kind]
+    a = gpu_render(rt, torch, p, variant=0)
+    b = gpu_render(rt, torch, p, variant=3)
+    same_variant_bar(a, b, precision)
+
+
+def same_variant_bar(a, b, precision):
+    """The two loops compile the same arithmetic separately, so the compiler
+    may fuse a different multiply-add here and there: FP64 results agree to
+    rounding, FP32 ones within the parity tolerances on all but the
+    ill-conditioned rays (the same bar as against the oracle)."""
+    ga, gb = a["rec"].reshape(-1), b["rec"].reshape(-1)
+    same = (ga["status"] == gb["status"]) & (ga["bounces"] == gb["bounces"])
+    dpos = np.abs(ga["pos"] - gb["pos"]).max(1)
+    ddir = np.linalg.norm(ga["dir"] - gb["dir"], axis=1)
+    exact = (dpos == 0) & (ddir == 0) & same
+    print(dict(exact=float(exact.mean()), same=float(same.mean()), dpos_max=float(dpos[same].max()),
+               ddir_max=float(ddir[same].max()), ddir_p999=float(np.percentile(ddir[same], 99.9))))
+    assert ga.size == gb.size and a["stats"]["rays"] == b["stats"]["rays"]
+    assert b["stats"]["sched_timeouts"] == 0
+    if precision == 1:
+        assert same.all() and dpos.max() <= 1e-10 and ddir.max() <= 1e-10
+        compare_images(a["rgb8"], b["rgb8"], max_frac=0.0)
+    else:
+        ok = same & (dpos <= POS_TOL) & (ddir <= DIR_TOL)
+        assert ok.mean() >= 0.995
+        compare_images(a["rgb8"], b["rgb8"], max_frac=0.001)
+
+
+@pytest.mark.parametrize("min_active", [1, 16, 32])
+def test_wave_main_config_equals_lane_loop(rt, torch, min_active):
+    """The full 512 x 512 x 4 cloaked render (the benchmark's dominant launch):
+    identical images and records for every setting of the wavefront loop."""
+    p = inputs.three_renders(inputs.config_main(precision=0))["cloak"]
+    a = gpu_render(rt, torch, p, variant=0, min_active=24)
+    b = gpu_render(rt, torch, p, variant=3, min_active=min_active)
+    same_variant_bar(a, b, 0)
+    assert b["stats"]["rays"] == 512 * 512 * 4
+    c = gpu_render(rt, torch, p, variant=3, min_active=24 if min_active != 24 else 16)
+    # within the wavefront loop the grouping of rays never changes a result
+    assert np.array_equal(b["rgb"], c["rgb"]) and np.array_equal(b["rec"]["dir"], c["rec"]["dir"])
+
+
+def test_wave_texture_and_pixel_list(rt, torch, orc):
+    """Textured background, a listed pixel subset and a ragged size through the wavefront loop."""
+    tex = inputs.value_noise(256, seed=6)
+    p = inputs.base_scene(width=37, height=29, spp=2, seed=6, background=1, tex_size=256, precision=0)
+    sc = rt.Scene(p, tex=tex)
+    sc.set_launch(3, 20)
+    pix_np = inputs.pixel_subset(29, 37, 200, seed=7)
+    pix = torch.tensor(pix_np, dtype=torch.int64, device="cuda")
+    rgb = torch.zeros((200, 3), dtype=torch.float32, device="cuda")
+    sc.render_pixels(pix, rgb)
+    torch.cuda.synchronize()
+    full = gpu_render(rt, torch, p, tex=tex, variant=3, min_active=28)
+    assert np.array_equal(rgb.cpu().numpy(), full["rgb"].reshape(-1, 3)[pix_np])
+    o_rgb = orc.render_pixels(orc.Scene(p, tex=tex), pix_np)
+    assert np.median(np.abs(rgb.cpu().numpy() - o_rgb)) < 1e-4
+
+
+def test_variant_not_compiled_is_rejected(rt):
+    sc = rt.Scene(inputs.base_scene(width=8, height=8, spp=1, precision=1))
+    with pytest.raises(Exception):
+        sc.set_launch(1, 0)          # per-lane register variants 1, 2 exist for FP32 RK4 only
+    sc.set_launch(3, 0)
+    assert sc.get_launch()["variant"] == 3

@@ -83,7 +83,8 @@ def test_budget_admission_and_busy(rt):
     assert e.value.code == rt.RT_EBUSY
     server.close()
     # a budget that holds one request at a time still serves every request
-    biggest = max(p["width"] * p["height"] * p["spp"] * 64 + p["width"] * p["height"] * 12 for _, p in reqs)
+    biggest = max(rt.request_bytes(p) for _, p in reqs)
+    assert biggest == max(p["width"] * p["height"] * (p["spp"] * 76 + 16) for _, p in reqs)
     server = rt.Server(budget_bytes=biggest, max_inflight=2)
     outs = [torch.zeros(rt.Scene(p).shape, dtype=torch.float32, device="cuda") for _, p in reqs]
     tickets = [server.submit(p, o) for (_, p), o in zip(reqs, outs)]

@@ -42,10 +42,10 @@ FLOP_PER_STEP = 105      # RK4 stage points, increments, compensated sums, event
 MUFU_PER_NEWTON = 4
 # DRAM bytes (read + write) of one cloaked-grating render launch of this
 # workload: dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture
-# (--set full, one launch) of the current render kernel.  The image writes
-# stay in L2, so nearly nothing reaches DRAM.  Set to None when the kernel
-# changes.
-TRAFFIC_CLOAK_BYTES = None
+# (--set full, one launch) of the current render kernel (wavefront loop).
+# The image, the per-sample colour scratch and the pixel counters mostly stay
+# in L2.  Set to None when the kernel changes.
+TRAFFIC_CLOAK_BYTES = 4645376
 
 
 def peaks():

@@ -888,11 +888,10 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
 // The integration step of the hot loop.
 // ------------------------------------------------------------------------
 template <class R, int INTEG>
-__device__ __forceinline__ void box_step(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf,
-                                         int& steps, LaneStats& st)
+__device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& b, int& phase,
+                                         int& surf, int& steps, LaneStats& st)
 {
-    const StepConst<R>& k = step_const<R>(sc);
-    if (steps >= sc.max_steps) {
+    if (steps >= max_steps) {
         phase = PH_GUARD;
         return;
     }
@@ -997,6 +996,7 @@ __device__ __forceinline__ uint8_t quantize8(float c)
 // samp_col (3 floats per sample) and count themselves in pix_cnt (one int per
 // pixel, zero at launch); the last one sums them in sample order.
 struct OneScene {
+    static constexpr bool kParamScene = true;    // the scene lives in the kernel parameters
     const DevScene& sc;
     float* rgb;
     uint8_t* rgb8;
@@ -1026,6 +1026,7 @@ struct OneScene {
 };
 
 struct ManyScenes {
+    static constexpr bool kParamScene = false;   // scenes in a device table
     const DevScene* scenes;
     const int64_t* offsets;          // n + 1 entries: first pixel of each scene
     const int64_t* soffsets;         // n + 1 entries: first sample of each scene
@@ -1146,7 +1147,10 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
             prof_iters += 1;
             prof_lanes += __popc(__ballot_sync(0xffffffffu, phase == PH_BOX));
 #endif
-            if (phase == PH_BOX) box_step<R, INTEG>(src.scene(C.scene), C, b, phase, surf, steps, st);
+            if (phase == PH_BOX) {
+                const DevScene& sc = src.scene(C.scene);
+                box_step<R, INTEG>(step_const<R>(sc), sc.max_steps, C, b, phase, surf, steps, st);
+            }
             if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
         }
 #if RT_PROFILE

@@ -271,11 +271,20 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                 steps = C.steps;
             }
             const int need = max(1, m1 - (32 - min_active));
-            for (int k = 0; k < kWaveTaskSteps; ++k) {
+            // step constants: read in place from the kernel parameters, or
+            // copied once per task from a scene table in device memory
+            const StepConst<R>* kp = &step_const<R>(sc);
+            StepConst<R> kc;
+            if constexpr (!Src::kParamScene) {
+                kc = *kp;
+                kp = &kc;
+            }
+            const int64_t max_steps = sc.max_steps;
+            for (int it = 0; it < kWaveTaskSteps; ++it) {
 #if RT_PROFILE
                 prof[2] += 1;
 #endif
-                if (phase == PH_BOX) box_step<R, INTEG>(sc, C, b, phase, surf, steps, st);
+                if (phase == PH_BOX) box_step<R, INTEG>(*kp, max_steps, C, b, phase, surf, steps, st);
                 if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
             }
             if (p >= 0) {

@@ -169,6 +169,9 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->cd.rtol = s->rtol; s->cd.atol = s->atol; s->cd.hmax = s->hmax;
     s->cf.kA = (float)s->kA; s->cf.A = (float)s->A; s->cf.h = (float)s->h; s->cf.ytop = (float)s->ytop;
     s->cf.E2 = (float)s->E2; s->cf.rtol = (float)s->rtol; s->cf.atol = (float)s->atol; s->cf.hmax = (float)s->hmax;
+    // FP32 Newton stop on W0: absolute, scaled by kA (|W| < kA in the cloak)
+    s->cf.w0tol = (float)(Mth<float>::kRel * s->kA);
+    s->cd.w0tol = Mth<double>::kRel * s->kA;
     for (int a = 0; a < 3; ++a) {
         s->ad.fr[a] = s->fr[a]; s->ad.ur[a] = s->ur[a]; s->ad.r[a] = s->r[a]; s->ad.Pb[a] = s->Pb[a];
         s->af.fr[a] = (float)s->fr[a]; s->af.ur[a] = (float)s->ur[a]; s->af.r[a] = (float)s->r[a];

@@ -27,6 +27,7 @@ template <class R>
 struct StepConst {
     R kA, A, h, ytop, E2;
     R rtol, atol, hmax;
+    R w0tol;     // FP32: Newton on W0 stops when |dW|^2 <= w0tol
 };
 
 // Constants of the straight segments to the background, in the path's precision.
@@ -85,8 +86,8 @@ template <> struct Mth<float> {
     static __device__ __forceinline__ void sincos(float a, float& s, float& c) { __sincosf(a, &s, &c); }
     static __device__ __forceinline__ float rint_(float x) { return rintf(x); }
     static __device__ __forceinline__ float sqrt_(float x) { return sqrtf(x); }
-    // stop when |dW|^2 <= kRel |W|: the next step would change W by about
-    // |dW|^2, a third of the FP32 resolution of W
+    // Newton on W0 stops when |dW|^2 <= kRel kA: the next step would change W
+    // by about |dW|^2 |W| / 2, below the FP32 resolution of the force
     static constexpr float kRel = 3.6e-8f;
     // the first-order continuation of W0 over dz is kept without a Newton step
     // when its error k^2 |W| n^3 |dz|^2 / 2 is below 1e-8 |W|
@@ -122,43 +123,67 @@ template <> struct Mth<double> {
 // whose Newton constant g''/2g' = -W/(2(1+W)) is small for the cloak's
 // |W| < kA < 1, by Newton steps with the derivative 1 + W of the current
 // iterate (g'(W) = 1 + W at the root).  Each step costs one exp, one
-// sin/cos pair and one reciprocal.  The reciprocal r = 1/(1+W) of the final
-// iterate is corrected to second order in the last step dW.
-// On return (wr, wi) = W and (rr, ri) = 1/(1+W); the result is the number of
-// Newton steps.
+// sin/cos pair and one reciprocal.
+// Stop: FP32 when |dW|^2 <= tol (tol = 3.6e-8 kA: the next step would move W
+// by about |dW|^2 |W|/2, below the FP32 resolution of the force); FP64 when
+// |dW|^2 <= 6e-17 |W|.  On return (wr, wi) = W and (rr, ri) = 1/(1+W): a fresh
+// reciprocal in FP32, the one of the last iterate corrected to second order
+// in the last step in FP64 (where a division costs more than the correction).
+// The result is the number of Newton steps.
 // ------------------------------------------------------------------------
 template <class R>
-__device__ __forceinline__ int w0_solve(R kA, R X, R y, R& wr, R& wi, R& rr, R& ri)
+__device__ __forceinline__ void newton_w0(R kA, R X, R y, R& wr, R& wi, R& rr, R& ri, R& dr, R& di)
 {
     const R L2E = R(kLog2e);
     const R KL2E = R(kTwoPi * kLog2e);
     const R I2PI = R(kInvTwoPi);
+    const R ar = R(1) + wr, ai = wi;
+    const R inv = Mth<R>::rcp(ar * ar + ai * ai);
+    rr = ar * inv;
+    ri = -ai * inv;
+    // q = kA exp(-(Re W + k y)) (cos(k X - Im W) + i sin(k X - Im W))
+    const R e = kA * Mth<R>::ex2(-(wr * L2E) - y * KL2E);
+    R a = X - wi * I2PI;
+    a -= Mth<R>::rint_(a);
+    R s, c;
+    Mth<R>::sincos2pi(a, s, c);
+    const R nr = wr + e * c, ni = wi + e * s;           // g(W)
+    dr = nr * rr - ni * ri;                              // dW = g(W)/(1+W)
+    di = nr * ri + ni * rr;
+    wr -= dr;
+    wi -= di;
+}
+
+template <class R>
+__device__ __forceinline__ bool w0_converged(R tol, R wr, R wi, R dr, R di)
+{
+    const R d2 = dr * dr + di * di;
+    if constexpr (sizeof(R) == 4) return d2 <= tol;
+    else return d2 * d2 <= (Mth<R>::kRel * Mth<R>::kRel) * (wr * wr + wi * wi);
+}
+
+template <class R>
+__device__ __forceinline__ int w0_solve(R kA, R tol, R X, R y, R& wr, R& wi, R& rr, R& ri)
+{
+    R dr, di;
     int it = 0;
     for (;;) {
+        newton_w0(kA, X, y, wr, wi, rr, ri, dr, di);
+        ++it;
+        if (w0_converged(tol, wr, wi, dr, di) || it >= Mth<R>::kMaxIt) break;
+    }
+    if constexpr (sizeof(R) == 4) {
         const R ar = R(1) + wr, ai = wi;
         const R inv = Mth<R>::rcp(ar * ar + ai * ai);
         rr = ar * inv;
         ri = -ai * inv;
-        // q = kA exp(-(Re W + k y)) (cos(k X - Im W) + i sin(k X - Im W))
-        const R e = kA * Mth<R>::ex2(-(wr * L2E) - y * KL2E);
-        R a = X - wi * I2PI;
-        a -= Mth<R>::rint_(a);
-        R s, c;
-        Mth<R>::sincos2pi(a, s, c);
-        const R nr = wr + e * c, ni = wi + e * s;           // g(W)
-        const R dr = nr * rr - ni * ri, di = nr * ri + ni * rr;  // dW = g(W)/(1+W)
-        wr -= dr;
-        wi -= di;
-        ++it;
-        const R d2 = dr * dr + di * di;
-        if (d2 * d2 <= (Mth<R>::kRel * Mth<R>::kRel) * (wr * wr + wi * wi) || it >= Mth<R>::kMaxIt) {
-            const R tr = rr * dr - ri * di, ti = rr * di + ri * dr;   // r dW
-            const R nrr = rr + (rr * tr - ri * ti), nri = ri + (rr * ti + ri * tr);
-            rr = nrr;
-            ri = nri;
-            return it;
-        }
+    } else {
+        const R tr = rr * dr - ri * di, ti = rr * di + ri * dr;   // r dW
+        const R nrr = rr + (rr * tr - ri * ti), nri = ri + (rr * ti + ri * tr);
+        rr = nrr;
+        ri = nri;
     }
+    return it;
 }
 
 // First-order continuation of W along a displacement (dx, dy):

@@ -114,9 +114,10 @@ static __device__ __noinline__ void w0_branch_fp64(double kA, double X, double y
 }
 
 template <class R>
-__device__ __forceinline__ void w0_eval(R kA, R X, R y, R& wr, R& wi, R& rr, R& ri, LaneStats& st)
+__device__ __forceinline__ void w0_eval(const StepConst<R>& k, R X, R y, R& wr, R& wi, R& rr, R& ri, LaneStats& st)
 {
-    st.newton += w0_solve(kA, X, y, wr, wi, rr, ri);
+    const R kA = k.kA;
+    st.newton += w0_solve(kA, k.w0tol, X, y, wr, wi, rr, ri);
     st.evals += 1;
     if constexpr (sizeof(R) == 4) {
         // |zeta + 1/e| < 1e-3 corresponds to |1 + W0|^2 < 2e * 1e-3
@@ -140,7 +141,8 @@ __device__ __forceinline__ void w0_eval(R kA, R X, R y, R& wr, R& wi, R& rr, R& 
 // the working precision (its error is about k^2 |W| n^3 |dz|^2 / 2); in that
 // case 1/(1+W) is continued to first order as well.
 template <class R>
-__device__ __forceinline__ void w0_continue(R kA, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri, LaneStats& st)
+__device__ __forceinline__ void w0_continue(const StepConst<R>& k, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri,
+                                            LaneStats& st)
 {
     const R n2 = rr * rr + ri * ri;
     const R dz2 = dx * dx + dy * dy;
@@ -155,7 +157,7 @@ __device__ __forceinline__ void w0_continue(R kA, R X, R y, R dx, R dy, R& wr, R
         st.evals += 1;
         return;
     }
-    w0_eval(kA, X, y, wr, wi, rr, ri, st);
+    w0_eval(k, X, y, wr, wi, rr, ri, st);
 }
 
 // ------------------------------------------------------------------------
@@ -177,23 +179,23 @@ __device__ __forceinline__ void kahan_add(R& s, R& c, R inc)
 // One RK4 step of size h from s (W0 solved and force known at s) into o;
 // o's W0 is continued to the end point but not solved.
 template <class R>
-__device__ __forceinline__ void rk4_step(R kA, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
+__device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
 {
     const R h2 = R(0.5) * h;
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     // stage 2 at r + h/2 p
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
-    w0_continue(kA, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
+    w0_continue(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
     R F2x, F2y;
     ray_force(wr, wi, rr, ri, F2x, F2y);
     // stage 3 at r + h/2 (p + h/2 F1), (h/2)^2 F1 away from stage 2
     const R X3 = s.X + h2 * (s.px + h2 * s.Fx), y3 = s.y + h2 * (s.py + h2 * s.Fy);
-    w0_continue(kA, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
+    w0_continue(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
     R F3x, F3y;
     ray_force(wr, wi, rr, ri, F3x, F3y);
     // stage 4 at r + h (p + h/2 F2)
     const R X4 = s.X + h * (s.px + h2 * F2x), y4 = s.y + h * (s.py + h2 * F2y);
-    w0_continue(kA, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
+    w0_continue(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
     R F4x, F4y;
     ray_force(wr, wi, rr, ri, F4x, F4y);
     // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
@@ -236,7 +238,8 @@ struct DPT {
 // (x, y, p_x, p_y).  The ODE is r' = p, p' = F(r): a stage momentum is
 // p + h sum a F and a stage position r + h sum a p_stage.
 template <class R>
-__device__ __forceinline__ void dp45_step(R kA, const Box<R>& s, R h, Box<R>& o, R e[4], LaneStats& st)
+__device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
+                                          LaneStats& st)
 {
     typedef DPT T;
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
@@ -244,7 +247,7 @@ __device__ __forceinline__ void dp45_step(R kA, const Box<R>& s, R h, Box<R>& o,
     const R F1x = s.Fx, F1y = s.Fy, P1x = s.px, P1y = s.py;
     auto stage = [&](R Px, R Py, R dXs, R dYs, R& Fx, R& Fy) {
         const R Xs = s.X + dXs, Ys = s.y + dYs;
-        w0_continue(kA, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, st);
+        w0_continue(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, st);
         ray_force(wr, wi, rr, ri, Fx, Fy);
         Xp = Xs;
         yp = Ys;
@@ -289,7 +292,7 @@ __device__ __forceinline__ void dp45_step(R kA, const Box<R>& s, R h, Box<R>& o,
     kahan_add(o.px, o.cpx, dPx);
     kahan_add(o.py, o.cpy, dPy);
     // force at the fifth-order point (first same as last)
-    w0_continue(kA, o.X, o.y, o.X - Xp, o.y - yp, wr, wi, rr, ri, st);
+    w0_continue(k, o.X, o.y, o.X - Xp, o.y - yp, wr, wi, rr, ri, st);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
     ray_force(wr, wi, rr, ri, o.Fx, o.Fy);
     // error estimate h sum (b - b*) k over the seven stages
@@ -304,13 +307,13 @@ __device__ __forceinline__ void dp45_step(R kA, const Box<R>& s, R h, Box<R>& o,
 // One step of the scene's integrator of size h from s into o (for event
 // location: Phi_{theta h}(s) is one step of size theta h).
 template <class R, int INTEG>
-__device__ __forceinline__ void integ_step(R kA, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
+__device__ __forceinline__ void integ_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
 {
     if constexpr (INTEG == RT_DP45) {
         R e[4];
-        dp45_step(kA, s, h, o, e, st);
+        dp45_step(k, s, h, o, e, st);
     } else {
-        rk4_step(kA, s, h, o, st);
+        rk4_step(k, s, h, o, st);
     }
 }
 
@@ -396,8 +399,8 @@ __device__ R locate_event(const StepConst<R>& k, const Box<R>& b, R h, int ev, b
     if (!(th > lo && th < hi)) th = R(0.5) * (lo + hi);
     int side = 0;
     for (int it = 0; it < Mth<R>::kEventIt; ++it) {
-        integ_step<R, INTEG>(k.kA, b, th * h, t, st);
-        w0_eval(k.kA, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
+        integ_step<R, INTEG>(k, b, th * h, t, st);
+        w0_eval(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
         const R g = event_g(k, ev, t);
         if (fabs(g) <= Mth<R>::kEventTol) return th;
         const R gd = on_surface ? g / th : g;
@@ -725,7 +728,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             b.y = C.y;
             b.z = C.z;
             b.wr = b.wi = R(0);
-            w0_eval(k.kA, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
+            w0_eval(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
             // Snell's law in FP64 (a few operations per entry): sqrt(n^2 - |p_t|^2)
             // is ill-conditioned near grazing incidence
             const double rr = (double)b.rr, ri = (double)b.ri;
@@ -817,8 +820,8 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
         }
     }
     if (last != ev_best) {
-        integ_step<R, INTEG>(k.kA, b, th_best * C.hs, t, st);
-        w0_eval(k.kA, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
+        integ_step<R, INTEG>(k, b, th_best * C.hs, t, st);
+        w0_eval(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
     }
     const R hc = b.hc;
     b = t;
@@ -887,27 +890,32 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
 // ------------------------------------------------------------------------
 // The integration step of the hot loop.
 // ------------------------------------------------------------------------
+// One step from s into o.  Accepted (phase stays PH_BOX): the new state is in
+// o.  A rejected Dormand-Prince attempt also leaves phase at PH_BOX, with o a
+// copy of s and a smaller next step.  A step that crosses a surface, goes
+// non-finite (PH_EVENT) or hits the step cap (PH_GUARD) leaves the state in s
+// and o undefined.  Writing into a second state lets the caller alternate
+// between two states instead of copying the new one back every step.
 template <class R, int INTEG>
-__device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& b, int& phase,
-                                         int& surf, int& steps, LaneStats& st)
+__device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& s,
+                                              Box<R>& o, int& phase, int& surf, int& steps, LaneStats& st)
 {
     if (steps >= max_steps) {
         phase = PH_GUARD;
         return;
     }
-    Box<R> s1;
     R hs;
     if constexpr (INTEG == RT_DP45) {
         // one attempt of an adaptive Dormand-Prince step; a rejected attempt
         // only shrinks the step
-        hs = b.hc;
+        hs = s.hc;
         R e[4];
-        dp45_step(k.kA, b, hs, s1, e, st);
+        dp45_step(k, s, hs, o, e, st);
         ++steps;
         st.steps++;
         const R scp = k.atol + k.rtol;                                    // positions (units of Lambda)
-        const R s2 = k.atol + k.rtol * fmax(fabs(b.px), fabs(s1.px));
-        const R s3 = k.atol + k.rtol * fmax(fabs(b.py), fabs(s1.py));
+        const R s2 = k.atol + k.rtol * fmax(fabs(s.px), fabs(o.px));
+        const R s3 = k.atol + k.rtol * fmax(fabs(s.py), fabs(o.py));
         const R q0 = e[0] / scp, q1 = e[1] / scp, q2 = e[2] / s2, q3 = e[3] / s3;
         const R err = Mth<R>::sqrt_(R(0.25) * (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3));
         R fac = (err > R(0)) ? R(0.9) * pow(err, R(-0.2)) : R(5);
@@ -919,28 +927,28 @@ __device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_step
                 phase = PH_EVENT;
                 return;
             }
-            b.hc = fmin(hs * fmin(fac, R(1)), k.hmax);
+            o = s;
+            o.hc = fmin(hs * fmin(fac, R(1)), k.hmax);
             return;
         }
-        s1.hc = fmin(hs * fac, k.hmax);
+        o.hc = fmin(hs * fac, k.hmax);
     } else {
         hs = k.h;
-        rk4_step(k.kA, b, hs, s1, st);
-        w0_eval(k.kA, s1.X, s1.y, s1.wr, s1.wi, s1.rr, s1.ri, st);
-        ray_force(s1.wr, s1.wi, s1.rr, s1.ri, s1.Fx, s1.Fy);
+        rk4_step(k, s, hs, o, st);
+        w0_eval(k, o.X, o.y, o.wr, o.wi, o.rr, o.ri, st);
+        ray_force(o.wr, o.wi, o.rr, o.ri, o.Fx, o.Fy);
         ++steps;
         st.steps++;
     }
-    const R gG = s1.y + s1.wr * R(kInvTwoPi);
-    const R gT = k.ytop - s1.y;
-    const R gXp = (k.E2 - s1.cx) - s1.X, gXm = (k.E2 + s1.cx) + s1.X;
-    const R gZp = k.E2 - s1.z, gZm = k.E2 + s1.z;
+    const R gG = o.y + o.wr * R(kInvTwoPi);
+    const R gT = k.ytop - o.y;
+    const R gXp = (k.E2 - o.cx) - o.X, gXm = (k.E2 + o.cx) + o.X;
+    const R gZp = k.E2 - o.z, gZm = k.E2 + o.z;
     if (gG >= R(0) && gT >= R(0) && gXp >= R(0) && gXm >= R(0) && gZp >= R(0) && gZm >= R(0)) {
-        b = s1;
         surf = EV_NONE;
         return;
     }
-    // crossed a surface (or went non-finite): the service pass locates it from b
+    // crossed a surface (or went non-finite): the service pass locates it from s
     C.g1[EV_GRATING] = gG;
     C.g1[EV_TOP] = gT;
     C.g1[EV_XP] = gXp;
@@ -948,8 +956,18 @@ __device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_step
     C.g1[EV_ZP] = gZp;
     C.g1[EV_ZM] = gZm;
     C.hs = hs;
-    if constexpr (INTEG == RT_DP45) b.hc = s1.hc;
+    if constexpr (INTEG == RT_DP45) s.hc = o.hc;
     phase = PH_EVENT;
+}
+
+// One step of b in place (the per-lane loop).
+template <class R, int INTEG>
+__device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& b, int& phase,
+                                         int& surf, int& steps, LaneStats& st)
+{
+    Box<R> o;
+    box_step_into<R, INTEG>(k, max_steps, C, b, o, phase, surf, steps, st);
+    if (phase == PH_BOX) b = o;
 }
 
 // ------------------------------------------------------------------------
@@ -1199,7 +1217,10 @@ __global__ void medium_kernel(double kA, double Lambda, const double* __restrict
     const R X = (R)(x - cxd), yy = (R)y;
     R wr = R(0), wi = R(0), rr, ri;
     LaneStats st = {0u, 0u, 0u, 0u};
-    w0_eval((R)kA, X, yy, wr, wi, rr, ri, st);
+    StepConst<R> k = {};
+    k.kA = (R)kA;
+    k.w0tol = (R)(Mth<R>::kRel * kA);
+    w0_eval(k, X, yy, wr, wi, rr, ri, st);
     R Fx, Fy;
     ray_force(wr, wi, rr, ri, Fx, Fy);
     out[5 * i + 0] = (double)wr;

@@ -1022,6 +1022,70 @@ int or_xcorr(const float* f, const float* g, int32_t H, int32_t W, int32_t C, in
     return 0;
 }
 
+/* The cross-correlation function C(di, dj) of Eq. 15 for pixel shifts
+   |di| <= max_di (rows), |dj| <= max_dj (columns), over the columns j0..j1-1
+   of both images (the finite-size photographs):
+     f' = f - <f>, g' = g - <g> over that window (Eq. 14);
+     C_c(di, dj) = sum f'(i, j) g'(i + di, j + dj) / sum f'(i, j)^2,
+   the numerator over the pixels where both lie in the window (the images have
+   no values outside it), the denominator over the whole window.  Per channel
+   and for the stacked channels (sum of numerators over sum of denominators).
+   out[((di + max_di) * (2 max_dj + 1) + (dj + max_dj)) * (C + 1) + c]. */
+int or_xcorr_map(const float* f, const float* g, int32_t H, int32_t W, int32_t C, int32_t j0, int32_t j1,
+                 int32_t max_di, int32_t max_dj, double* out)
+{
+    const int ndj = 2 * max_dj + 1;
+    double* mf = (double*)calloc((size_t)C, sizeof(double));
+    double* mg = (double*)calloc((size_t)C, sizeof(double));
+    double* den = (double*)calloc((size_t)C, sizeof(double));
+    if (!mf || !mg || !den) { free(mf); free(mg); free(den); return -1; }
+    const double cnt = (double)H * (double)(j1 - j0);
+    for (int c = 0; c < C; ++c) {
+        double sf = 0.0, sg = 0.0;
+        for (int i = 0; i < H; ++i)
+            for (int j = j0; j < j1; ++j) {
+                sf += f[((int64_t)i * W + j) * C + c];
+                sg += g[((int64_t)i * W + j) * C + c];
+            }
+        mf[c] = sf / cnt;                                             /* Eq. 14 */
+        mg[c] = sg / cnt;
+        double d = 0.0;
+        for (int i = 0; i < H; ++i)
+            for (int j = j0; j < j1; ++j) {
+                const double a = f[((int64_t)i * W + j) * C + c] - mf[c];
+                d += a * a;                                           /* Eq. 15 denominator */
+            }
+        den[c] = d;
+    }
+    for (int di = -max_di; di <= max_di; ++di)
+        for (int dj = -max_dj; dj <= max_dj; ++dj) {
+            double* o = out + ((int64_t)(di + max_di) * ndj + (dj + max_dj)) * (C + 1);
+            double num_all = 0.0, den_all = 0.0;
+            for (int c = 0; c < C; ++c) {
+                double num = 0.0;
+                for (int i = 0; i < H; ++i) {
+                    const int ig = i + di;
+                    if (ig < 0 || ig >= H) continue;
+                    for (int j = j0; j < j1; ++j) {
+                        const int jg = j + dj;
+                        if (jg < j0 || jg >= j1) continue;
+                        const double a = f[((int64_t)i * W + j) * C + c] - mf[c];
+                        const double b = g[((int64_t)ig * W + jg) * C + c] - mg[c];
+                        num += a * b;                                 /* Eq. 15 numerator */
+                    }
+                }
+                o[c] = num / den[c];
+                num_all += num;
+                den_all += den[c];
+            }
+            o[C] = num_all / den_all;
+        }
+    free(mf);
+    free(mg);
+    free(den);
+    return 0;
+}
+
 /* Columns of a width-W image whose pixel-centre horizontal angle lies within
    the horizontal field of view fov (degrees) about the image centre. */
 int or_fov_columns(int32_t W, double hfov_deg, double fov_deg, int32_t* j0, int32_t* j1)

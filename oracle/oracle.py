@@ -88,6 +88,8 @@ def lib():
         L.or_quantize.argtypes = [C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_uint8)]
         L.or_xcorr.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32,
                                C.c_int32, C.c_int32, dp]
+        L.or_xcorr_map.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32,
+                                   C.c_int32, C.c_int32, C.c_int32, C.c_int32, dp]
         L.or_fov_columns.argtypes = [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32)]
         L.or_max_threads.restype = C.c_int
@@ -230,6 +232,22 @@ def xcorr(f, g, j0: int, j1: int) -> np.ndarray:
     out = np.zeros(Cc + 1)
     lib().or_xcorr(f.ctypes.data_as(C.POINTER(C.c_float)), g.ctypes.data_as(C.POINTER(C.c_float)),
                    H, W, Cc, j0, j1, _dp(out))
+    return out
+
+
+def xcorr_map(f, g, j0: int, j1: int, max_di: int, max_dj: int) -> np.ndarray:
+    """C(di, dj) of Eq. 15 for |di| <= max_di, |dj| <= max_dj over columns j0..j1-1:
+    array (2 max_di + 1, 2 max_dj + 1, channels + 1), the last entry the stacked channels."""
+    f = np.ascontiguousarray(np.asarray(f, dtype=np.float32))
+    g = np.ascontiguousarray(np.asarray(g, dtype=np.float32))
+    if f.ndim == 2:
+        f = f[..., None]
+        g = g[..., None]
+    H, W, Cc = f.shape
+    out = np.zeros((2 * max_di + 1, 2 * max_dj + 1, Cc + 1))
+    if lib().or_xcorr_map(f.ctypes.data_as(C.POINTER(C.c_float)), g.ctypes.data_as(C.POINTER(C.c_float)),
+                          H, W, Cc, j0, j1, max_di, max_dj, _dp(out)):
+        raise MemoryError("oracle: allocation failed")
     return out
 
 

@@ -322,6 +322,7 @@ def run_gpu(args):
     d2h = sum(h.numel() * 4 for h in host.values()) + hc.numel() * 8 + hl.numel() * 8
     h2d = len(step.scenes) * 512      # scene parameters travel with each launch (DevScene by value)
 
+    xmap = bench_xcorr_map(rt, torch, step, stream, clock_mhz)
     batch = None if args.no_batch else bench_batch(rt, torch, stream)
     serving = None if args.no_serving else bench_serving(rt, torch)
 
@@ -347,6 +348,7 @@ def run_gpu(args):
         "cpu_baseline": cpu,
         "e2e": {"value": round(rays_per_step / e2e_s / 1e6, 3), "unit": "Mrays/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "xcorr_map": xmap,
         "batched_64_scenes": batch,
         "serving": serving,
         "gpu_launches": step.launches * args.steps,
@@ -357,6 +359,39 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def bench_xcorr_map(rt, torch, step, stream, clock_mhz: float) -> dict:
+    """C(di, dj) of Eq. 15 for shifts up to +-32 pixels between the step's
+    flat-mirror and cloaked renders (512 x 512 x 3, FOV 50 deg): time per map,
+    algorithmic FP32 work (one multiply-add per product of the overlaps) and
+    the peak with its shift."""
+    f, g = step.img["mirror"], step.img["cloak"]
+    H, W, Cc = f.shape
+    md = 32
+    out = torch.empty((2 * md + 1, 2 * md + 1, Cc + 1), dtype=torch.float64, device="cuda")
+    peak = torch.empty(3, dtype=torch.float64, device="cuda")
+    with torch.cuda.stream(stream):
+        rt.xcorr_map([(f, g)], 50.0, 50.0, md, md, out=out, peak=peak, stream=stream)
+    torch.cuda.synchronize()
+    n = 5
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(n):
+            rt.xcorr_map([(f, g)], 50.0, 50.0, md, md, out=out, peak=peak, stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    j0, j1 = 0, W      # FOV 50 deg is the whole width of a 50 deg camera
+    wc = j1 - j0
+    prods = sum((H - abs(a)) * (wc - abs(b)) for a in range(-md, md + 1) for b in range(-md, md + 1)) * Cc
+    tflops = 2.0 * prods / (ms * 1e-3) / 1e12
+    pk = peak.cpu().numpy()
+    return {"shifts": f"+-{md} x +-{md}", "ms": round(ms, 3), "achieved_tflops": round(tflops, 2),
+            "frac_fp32_peak": round(tflops / (152 * 128 * 2 * clock_mhz * 1e6 / 1e12), 3),
+            "C00_stacked": round(float(out[md, md, Cc].item()), 6),
+            "peak": {"C": round(float(pk[0]), 6), "di": int(pk[1]), "dj": int(pk[2])}}
 
 
 def bench_batch(rt, torch, stream) -> dict:

@@ -346,6 +346,30 @@ int rt_xcorr_noalloc(const float* d_f, const float* d_g, int32_t height, int32_t
                      const double* fov_deg, int32_t n_fov, double hfov_deg, double* d_out, void* stream);
 
 /*
+ * rt_xcorr_map: the cross-correlation function C(di, dj) of Eq. 15 over pixel
+ * shifts (Sec. 5), its peak and its mean over several reference pairs.
+ * d_f[p], d_g[p] (host arrays of n_pairs device pointers, 1..64 pairs): the
+ * reference and compared images, each height x width x channels float.  The
+ * window is the columns within the field of view fov_deg (as in rt_xcorr) of
+ * both images, which have no values outside it:
+ *   f' = f - <f>, g' = g - <g> with the means over the window (Eq. 14),
+ *   C_c(di, dj) = sum f'(i, j) g'(i + di, j + dj) / sum f'(i, j)^2,
+ * the numerator over the pixels where both lie in the window, the denominator
+ * over the whole window; di is a row shift, dj a column shift, |di| <=
+ * max_di, |dj| <= max_dj (0..64).  Per channel and for the stacked channels
+ * (sum of numerators over sum of denominators), averaged over the pairs.
+ * d_map (device) receives (2 max_di + 1) x (2 max_dj + 1) x (channels + 1)
+ * doubles, row-major in (di, dj, channel); d_peak (device, nullable) receives
+ * the largest stacked value of the mean map and its (di, dj) as three
+ * doubles, the first in row-major order among equal values.  RT_EINVAL for an
+ * empty window or arguments out of range.  Asynchronous; its scratch is
+ * allocated and freed in stream order on `stream`.
+ */
+int rt_xcorr_map(const float* const* d_f, const float* const* d_g, int32_t n_pairs, int32_t height, int32_t width,
+                 int32_t channels, double fov_deg, double hfov_deg, int32_t max_di, int32_t max_dj, double* d_map,
+                 double* d_peak, void* stream);
+
+/*
  * rt_eval_medium: W0, n and the ray force grad(n^2)/2 at npoints points
  * (device d_xy: x0,y0,x1,y1,..., world units) for grating period Lambda and
  * amplitude A (Eqs. 1, 12, 13).  d_out gets per point

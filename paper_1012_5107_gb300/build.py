@@ -16,7 +16,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgratingrt.so")
-SOURCES = ["rt_api.cu", "rt_render.cu", "rt_batch.cu", "rt_server.cu", "rt_xcorr.cu", "rt_xcorr_noalloc.cu"]
+SOURCES = ["rt_api.cu", "rt_render.cu", "rt_batch.cu", "rt_server.cu", "rt_xcorr.cu", "rt_xcorr_noalloc.cu",
+           "rt_xcorr_map.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
 

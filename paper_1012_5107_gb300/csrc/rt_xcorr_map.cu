@@ -1,0 +1,233 @@
+// rt_xcorr_map.cu -- the cross-correlation function C(di, dj) of Eq. 15 over
+// pixel shifts, its peak and its mean over several reference pairs (Sec. 5).
+//
+// Pass 1 (one block per pair and channel) forms, over the field-of-view window
+// of columns j0..j1-1, the means of Eq. 14 and the denominator
+// sum (f - <f>)^2 of Eq. 15 in FP64.
+// Pass 2 is a direct correlation in tiles: a block owns 8 x 32 shifts
+// (di, dj) and a chunk of 32 image rows of one pair and channel; per row it
+// stages the window's f row and the 8 g rows the shifts need (zero outside
+// the window, where the finite photographs have no values) in shared memory,
+// and every thread accumulates its shift's products over the chunk with FP32
+// FMA.  A warp reads one f value (broadcast) and 32 consecutive g values per
+// step, so the shared-memory reads are free of bank conflicts.
+// Pass 3 sums the chunks in FP64, divides by the denominators, stacks the
+// channels (sum of numerators over sum of denominators) and averages the maps
+// of the pairs; pass 4 finds the peak of the stacked mean map and its shift.
+#include <cmath>
+#include <vector>
+
+#include "rt_internal.h"
+
+namespace grt {
+
+constexpr int kMapTDI = 8;        // shifts in di per block
+constexpr int kMapTDJ = 32;       // shifts in dj per block (one warp)
+constexpr int kMapTW = 128;       // columns staged per step
+constexpr int kMapRows = 32;      // image rows per chunk
+constexpr int kMapBlock = kMapTDI * kMapTDJ;
+constexpr int kMapMaxShift = 64;
+constexpr int kMapMaxPairs = 64;
+
+struct MapImages {
+    const float* f[kMapMaxPairs];
+    const float* g[kMapMaxPairs];
+};
+
+__global__ void __launch_bounds__(256) xmap_moments(MapImages im, int H, int W, int C, int j0, int j1,
+                                                    double* __restrict__ stats)
+{
+    const int pair = blockIdx.x / C, c = blockIdx.x % C;
+    const float* f = im.f[pair];
+    const float* g = im.g[pair];
+    const int wc = j1 - j0;
+    const int64_t n = (int64_t)H * wc;
+    double sf = 0.0, sg = 0.0, sff = 0.0;
+    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+        const int i = (int)(t / wc), j = j0 + (int)(t % wc);
+        const double a = __ldg(f + ((int64_t)i * W + j) * C + c), b = __ldg(g + ((int64_t)i * W + j) * C + c);
+        sf += a;
+        sg += b;
+        sff += a * a;
+    }
+    __shared__ double red[3][8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    double v[3] = {sf, sg, sff};
+    for (int q = 0; q < 3; ++q) {
+        double x = v[q];
+        for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+        if (lane == 0) red[q][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t[3] = {0.0, 0.0, 0.0};
+        for (int q = 0; q < 3; ++q)
+            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[q] += red[q][w];
+        const double N = (double)n;
+        const double mf = t[0] / N, mg = t[1] / N;          // Eq. 14
+        stats[3 * blockIdx.x + 0] = mf;
+        stats[3 * blockIdx.x + 1] = mg;
+        stats[3 * blockIdx.x + 2] = t[2] - t[0] * mf;       // sum (f - <f>)^2, Eq. 15 denominator
+    }
+}
+
+__global__ void __launch_bounds__(kMapBlock) xmap_tiles(MapImages im, const double* __restrict__ stats, int H, int W,
+                                                        int C, int j0, int j1, int max_di, int max_dj, int nchunks,
+                                                        double* __restrict__ partial)
+{
+    __shared__ float f_s[kMapTW];
+    __shared__ float g_s[kMapTDI][kMapTW + kMapTDJ];
+    const int ndi = 2 * max_di + 1, ndj = 2 * max_dj + 1;
+    const int tiles_dj = (ndj + kMapTDJ - 1) / kMapTDJ;
+    const int tdi = blockIdx.x / tiles_dj, tdj = blockIdx.x % tiles_dj;
+    const int chunk = blockIdx.y;
+    const int pc = blockIdx.z;
+    const int pair = pc / C, c = pc % C;
+    const float* f = im.f[pair];
+    const float* g = im.g[pair];
+    const float mf = (float)stats[3 * pc + 0], mg = (float)stats[3 * pc + 1];
+    const int di_lo = -max_di + tdi * kMapTDI, dj_lo = -max_dj + tdj * kMapTDJ;
+    const int ty = threadIdx.x / kMapTDJ, tx = threadIdx.x % kMapTDJ;
+    const int i0 = chunk * kMapRows, i1 = min(H, i0 + kMapRows);
+    float acc = 0.0f;
+    for (int i = i0; i < i1; ++i) {
+        for (int jt = j0; jt < j1; jt += kMapTW) {
+            for (int q = threadIdx.x; q < kMapTW; q += kMapBlock) {
+                const int j = jt + q;
+                f_s[q] = (j < j1) ? __ldg(f + ((int64_t)i * W + j) * C + c) - mf : 0.0f;
+            }
+            for (int q = threadIdx.x; q < kMapTDI * (kMapTW + kMapTDJ); q += kMapBlock) {
+                const int r = q / (kMapTW + kMapTDJ), col = q % (kMapTW + kMapTDJ);
+                const int ig = i + di_lo + r, jg = jt + dj_lo + col;
+                g_s[r][col] = (ig >= 0 && ig < H && jg >= j0 && jg < j1)
+                                  ? __ldg(g + ((int64_t)ig * W + jg) * C + c) - mg
+                                  : 0.0f;
+            }
+            __syncthreads();
+#pragma unroll 16
+            for (int q = 0; q < kMapTW; ++q) acc = fmaf(f_s[q], g_s[ty][q + tx], acc);
+            __syncthreads();
+        }
+    }
+    const int di = di_lo + ty, dj = dj_lo + tx;
+    if (di <= max_di && dj <= max_dj) {
+        const int s = (di + max_di) * ndj + (dj + max_dj);
+        partial[((int64_t)pc * nchunks + chunk) * ((int64_t)ndi * ndj) + s] = (double)acc;
+    }
+}
+
+__global__ void __launch_bounds__(256) xmap_finish(const double* __restrict__ partial,
+                                                   const double* __restrict__ stats, int n_pairs, int C, int nchunks,
+                                                   int nshift, double* __restrict__ out)
+{
+    const int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= nshift) return;
+    double mean[5] = {0.0, 0.0, 0.0, 0.0, 0.0};
+    for (int p = 0; p < n_pairs; ++p) {
+        double num_all = 0.0, den_all = 0.0;
+        for (int c = 0; c < C; ++c) {
+            const int pc = p * C + c;
+            double num = 0.0;
+            for (int k = 0; k < nchunks; ++k) num += partial[((int64_t)pc * nchunks + k) * nshift + s];
+            const double den = stats[3 * pc + 2];
+            mean[c] += num / den;
+            num_all += num;
+            den_all += den;
+        }
+        mean[C] += num_all / den_all;
+    }
+    for (int c = 0; c <= C; ++c) out[(int64_t)s * (C + 1) + c] = mean[c] / (double)n_pairs;
+}
+
+// Peak of the stacked-channel map: largest value, the first in row-major
+// order (di, then dj ascending) among equal ones.
+__global__ void __launch_bounds__(1024) xmap_peak(const double* __restrict__ map, int C, int max_di, int max_dj,
+                                                  double* __restrict__ peak)
+{
+    const int ndj = 2 * max_dj + 1, nshift = (2 * max_di + 1) * ndj;
+    double best = -INFINITY;
+    int bi = nshift;
+    for (int s = threadIdx.x; s < nshift; s += blockDim.x) {
+        const double v = map[(int64_t)s * (C + 1) + C];
+        if (v > best || (v == best && s < bi)) { best = v; bi = s; }
+    }
+    __shared__ double sv[32];
+    __shared__ int si[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        const double ov = __shfl_down_sync(0xffffffffu, best, o);
+        const int oi = __shfl_down_sync(0xffffffffu, bi, o);
+        if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+    }
+    if (lane == 0) { sv[warp] = best; si[warp] = bi; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w)
+            if (sv[w] > best || (sv[w] == best && si[w] < bi)) { best = sv[w]; bi = si[w]; }
+        peak[0] = best;
+        peak[1] = (double)(bi / ndj - max_di);
+        peak[2] = (double)(bi % ndj - max_dj);
+    }
+}
+
+}  // namespace grt
+
+using namespace grt;
+
+extern "C" int rt_xcorr_map(const float* const* d_f, const float* const* d_g, int32_t n_pairs, int32_t height,
+                            int32_t width, int32_t channels, double fov_deg, double hfov_deg, int32_t max_di,
+                            int32_t max_dj, double* d_map, double* d_peak, void* stream)
+{
+    if (!d_f || !d_g || !d_map) { set_error("null pointer argument"); return RT_EINVAL; }
+    if (n_pairs < 1 || n_pairs > kMapMaxPairs) { set_error("n_pairs must be 1..%d", kMapMaxPairs); return RT_EINVAL; }
+    for (int p = 0; p < n_pairs; ++p)
+        if (!d_f[p] || !d_g[p]) { set_error("image pointer of pair %d is NULL", p); return RT_EINVAL; }
+    if (height < 1 || width < 1) { set_error("height and width must be >= 1"); return RT_EINVAL; }
+    if (channels < 1 || channels > 4) { set_error("channels must be 1..4"); return RT_EINVAL; }
+    if (max_di < 0 || max_di > kMapMaxShift || max_dj < 0 || max_dj > kMapMaxShift) {
+        set_error("max_di and max_dj must be 0..%d", kMapMaxShift);
+        return RT_EINVAL;
+    }
+    if (!(hfov_deg > 0.0 && hfov_deg < 180.0)) { set_error("hfov_deg must be in (0, 180)"); return RT_EINVAL; }
+    if (!(fov_deg >= 0.0)) { set_error("fov_deg must be >= 0"); return RT_EINVAL; }
+    Windows win;
+    fov_windows(width, hfov_deg, &fov_deg, 1, &win);
+    const int j0 = win.j0[0], j1 = win.j1[0];
+    if (j1 <= j0) { set_error("the field of view holds no pixel column"); return RT_EINVAL; }
+    MapImages im;
+    for (int p = 0; p < n_pairs; ++p) { im.f[p] = d_f[p]; im.g[p] = d_g[p]; }
+    const int ndi = 2 * max_di + 1, ndj = 2 * max_dj + 1, nshift = ndi * ndj;
+    const int nchunks = (height + kMapRows - 1) / kMapRows;
+    const int npc = n_pairs * channels;
+    cudaStream_t st = (cudaStream_t)stream;
+    double* stats = nullptr;
+    double* partial = nullptr;
+    cudaError_t e = cudaMallocAsync((void**)&stats, sizeof(double) * 3 * npc, st);
+    if (e == cudaSuccess)
+        e = cudaMallocAsync((void**)&partial, sizeof(double) * (size_t)npc * nchunks * nshift, st);
+    if (e == cudaSuccess) {
+        xmap_moments<<<npc, 256, 0, st>>>(im, height, width, channels, j0, j1, stats);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        const dim3 grid(((ndi + kMapTDI - 1) / kMapTDI) * ((ndj + kMapTDJ - 1) / kMapTDJ), nchunks, npc);
+        xmap_tiles<<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj, nchunks,
+                                              partial);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        xmap_finish<<<(nshift + 255) / 256, 256, 0, st>>>(partial, stats, n_pairs, channels, nchunks, nshift, d_map);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && d_peak) {
+        xmap_peak<<<1, 1024, 0, st>>>(d_map, channels, max_di, max_dj, d_peak);
+        e = cudaGetLastError();
+    }
+    if (partial) cudaFreeAsync(partial, st);
+    if (stats) cudaFreeAsync(stats, st);
+    if (e != cudaSuccess) {
+        set_error("rt_xcorr_map: %s", cudaGetErrorString(e));
+        return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
+    }
+    return RT_OK;
+}

@@ -81,7 +81,7 @@ EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels
            "rt_batch_get_launch", "rt_batch_autotune",
            "rt_validate_desc", "rt_request_bytes", "rt_server_create", "rt_server_destroy", "rt_submit", "rt_poll",
            "rt_server_stats",
-           "rt_xcorr", "rt_xcorr_noalloc", "rt_eval_medium", "rt_last_error", "rt_version"]
+           "rt_xcorr", "rt_xcorr_noalloc", "rt_xcorr_map", "rt_eval_medium", "rt_last_error", "rt_version"]
 
 
 def lib() -> C.CDLL:
@@ -116,6 +116,8 @@ def lib() -> C.CDLL:
                            C.c_double, vp, vp]
     L.rt_xcorr_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                                    C.c_double, vp, vp]
+    L.rt_xcorr_map.argtypes = [C.POINTER(vp), C.POINTER(vp), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                               C.c_double, C.c_double, C.c_int32, C.c_int32, vp, vp, vp]
     L.rt_eval_medium.argtypes = [C.c_int32, C.c_double, C.c_double, vp, C.c_int64, vp, vp]
     L.rt_validate_desc.argtypes = [C.POINTER(SceneDesc)]
     L.rt_request_bytes.argtypes = [C.POINTER(SceneDesc), C.POINTER(C.c_uint64)]
@@ -303,6 +305,33 @@ def xcorr(f, g, fov_deg, hfov_deg: float, out=None, stream=None):
     _check(lib().rt_xcorr(_ptr(f), _ptr(g), H, W, Cc, fov, len(fov_deg), float(hfov_deg), _ptr(out),
                           _stream(stream)))
     return out
+
+
+def xcorr_map(pairs, fov_deg: float, hfov_deg: float, max_di: int, max_dj: int, out=None, peak=None,
+              stream=None):
+    """C(di, dj) of Eq. 15 over pixel shifts, averaged over the (f, g) image
+    pairs (rt_xcorr_map): returns the float64 CUDA map (2 max_di + 1,
+    2 max_dj + 1, C + 1) and the peak tensor (value, di, dj) of its stacked
+    channels."""
+    import torch
+    fs, gs = [], []
+    for f, g in pairs:
+        if f.dim() == 2:
+            f = f.unsqueeze(-1)
+            g = g.unsqueeze(-1)
+        fs.append(f)
+        gs.append(g)
+    H, W, Cc = fs[0].shape
+    n = len(fs)
+    fp = (C.c_void_p * n)(*[_ptr(t) for t in fs])
+    gp = (C.c_void_p * n)(*[_ptr(t) for t in gs])
+    if out is None:
+        out = torch.empty((2 * max_di + 1, 2 * max_dj + 1, Cc + 1), dtype=torch.float64, device=fs[0].device)
+    if peak is None:
+        peak = torch.empty(3, dtype=torch.float64, device=fs[0].device)
+    _check(lib().rt_xcorr_map(fp, gp, n, H, W, Cc, float(fov_deg), float(hfov_deg), int(max_di), int(max_dj),
+                              _ptr(out), _ptr(peak), _stream(stream)))
+    return out, peak
 
 
 def xcorr_noalloc(f, g, fov_deg, hfov_deg: float, out=None, stream=None):

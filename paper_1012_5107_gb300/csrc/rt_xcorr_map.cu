@@ -4,13 +4,12 @@
 // Pass 1 (one block per pair and channel) forms, over the field-of-view window
 // of columns j0..j1-1, the means of Eq. 14 and the denominator
 // sum (f - <f>)^2 of Eq. 15 in FP64.
-// Pass 2 is a direct correlation in tiles: a block owns 8 x 32 shifts
+// Pass 2 is a direct correlation in tiles: a block owns 8 x 32 R shifts
 // (di, dj) and a chunk of 32 image rows of one pair and channel; per row it
 // stages the window's f row and the 8 g rows the shifts need (zero outside
 // the window, where the finite photographs have no values) in shared memory,
-// and every thread accumulates its shift's products over the chunk with FP32
-// FMA.  A warp reads one f value (broadcast) and 32 consecutive g values per
-// step, so the shared-memory reads are free of bank conflicts.
+// and every thread accumulates its R shifts' products over the chunk with
+// FP32 FMA (see xmap_tiles).
 // Pass 3 sums the chunks in FP64, divides by the denominators, stacks the
 // channels (sum of numerators over sum of denominators) and averages the maps
 // of the pairs; pass 4 finds the peak of the stacked mean map and its shift.
@@ -71,14 +70,22 @@ __global__ void __launch_bounds__(256) xmap_moments(MapImages im, int H, int W, 
     }
 }
 
+// One block: 8 row shifts (one per warp) x 32 R column shifts, lane l owning
+// the R consecutive column shifts dj_lo + l R + k.  Along a staged row a lane
+// keeps the R g values its shifts need in registers and slides them by one
+// per column, so each step costs one broadcast f load and one g load for R
+// FMAs; R is odd, so the lanes' g loads (stride R) hit distinct banks.
+template <int R>
 __global__ void __launch_bounds__(kMapBlock) xmap_tiles(MapImages im, const double* __restrict__ stats, int H, int W,
                                                         int C, int j0, int j1, int max_di, int max_dj, int nchunks,
                                                         double* __restrict__ partial)
 {
+    constexpr int TJ = kMapTDJ * R;              // column shifts per block
+    constexpr int GW = kMapTW + TJ;              // staged g columns per row
     __shared__ float f_s[kMapTW];
-    __shared__ float g_s[kMapTDI][kMapTW + kMapTDJ];
+    __shared__ float g_s[kMapTDI][GW];
     const int ndi = 2 * max_di + 1, ndj = 2 * max_dj + 1;
-    const int tiles_dj = (ndj + kMapTDJ - 1) / kMapTDJ;
+    const int tiles_dj = (ndj + TJ - 1) / TJ;
     const int tdi = blockIdx.x / tiles_dj, tdj = blockIdx.x % tiles_dj;
     const int chunk = blockIdx.y;
     const int pc = blockIdx.z;
@@ -86,33 +93,50 @@ __global__ void __launch_bounds__(kMapBlock) xmap_tiles(MapImages im, const doub
     const float* f = im.f[pair];
     const float* g = im.g[pair];
     const float mf = (float)stats[3 * pc + 0], mg = (float)stats[3 * pc + 1];
-    const int di_lo = -max_di + tdi * kMapTDI, dj_lo = -max_dj + tdj * kMapTDJ;
+    const int di_lo = -max_di + tdi * kMapTDI, dj_lo = -max_dj + tdj * TJ;
     const int ty = threadIdx.x / kMapTDJ, tx = threadIdx.x % kMapTDJ;
     const int i0 = chunk * kMapRows, i1 = min(H, i0 + kMapRows);
-    float acc = 0.0f;
+    float acc[R];
+#pragma unroll
+    for (int k = 0; k < R; ++k) acc[k] = 0.0f;
+    const float* gr = &g_s[ty][tx * R];
     for (int i = i0; i < i1; ++i) {
         for (int jt = j0; jt < j1; jt += kMapTW) {
             for (int q = threadIdx.x; q < kMapTW; q += kMapBlock) {
                 const int j = jt + q;
                 f_s[q] = (j < j1) ? __ldg(f + ((int64_t)i * W + j) * C + c) - mf : 0.0f;
             }
-            for (int q = threadIdx.x; q < kMapTDI * (kMapTW + kMapTDJ); q += kMapBlock) {
-                const int r = q / (kMapTW + kMapTDJ), col = q % (kMapTW + kMapTDJ);
+            for (int q = threadIdx.x; q < kMapTDI * GW; q += kMapBlock) {
+                const int r = q / GW, col = q % GW;
                 const int ig = i + di_lo + r, jg = jt + dj_lo + col;
                 g_s[r][col] = (ig >= 0 && ig < H && jg >= j0 && jg < j1)
                                   ? __ldg(g + ((int64_t)ig * W + jg) * C + c) - mg
                                   : 0.0f;
             }
             __syncthreads();
-#pragma unroll 16
-            for (int q = 0; q < kMapTW; ++q) acc = fmaf(f_s[q], g_s[ty][q + tx], acc);
+            float win[R];
+#pragma unroll
+            for (int k = 0; k < R; ++k) win[k] = gr[k];
+#pragma unroll 32
+            for (int q = 0; q < kMapTW; ++q) {
+                const float fv = f_s[q];
+#pragma unroll
+                for (int k = 0; k < R; ++k) acc[k] = fmaf(fv, win[k], acc[k]);
+#pragma unroll
+                for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
+                win[R - 1] = gr[q + R];
+            }
             __syncthreads();
         }
     }
-    const int di = di_lo + ty, dj = dj_lo + tx;
-    if (di <= max_di && dj <= max_dj) {
-        const int s = (di + max_di) * ndj + (dj + max_dj);
-        partial[((int64_t)pc * nchunks + chunk) * ((int64_t)ndi * ndj) + s] = (double)acc;
+    const int di = di_lo + ty;
+#pragma unroll
+    for (int k = 0; k < R; ++k) {
+        const int dj = dj_lo + tx * R + k;
+        if (di <= max_di && dj <= max_dj) {
+            const int s = (di + max_di) * ndj + (dj + max_dj);
+            partial[((int64_t)pc * nchunks + chunk) * ((int64_t)ndi * ndj) + s] = (double)acc[k];
+        }
     }
 }
 
@@ -210,9 +234,18 @@ extern "C" int rt_xcorr_map(const float* const* d_f, const float* const* d_g, in
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        const dim3 grid(((ndi + kMapTDI - 1) / kMapTDI) * ((ndj + kMapTDJ - 1) / kMapTDJ), nchunks, npc);
-        xmap_tiles<<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj, nchunks,
-                                              partial);
+        // column shifts per lane: the smallest odd R with 32 R >= ndj (1, 3 or 5)
+        const int R = ndj <= kMapTDJ ? 1 : (ndj <= 3 * kMapTDJ ? 3 : 5);
+        const dim3 grid(((ndi + kMapTDI - 1) / kMapTDI) * ((ndj + kMapTDJ * R - 1) / (kMapTDJ * R)), nchunks, npc);
+        if (R == 1)
+            xmap_tiles<1><<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj,
+                                                      nchunks, partial);
+        else if (R == 3)
+            xmap_tiles<3><<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj,
+                                                      nchunks, partial);
+        else
+            xmap_tiles<5><<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj,
+                                                      nchunks, partial);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

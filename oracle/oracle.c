@@ -24,7 +24,13 @@
  *     integrator step from the state s at the start of the step;
  *   - the cloak is a box |x|,|z| <= E/2, -A <= y <= -A + H with n from Eq. 1
  *     inside and n = 1 outside; at its faces Snell's law acts on p (tangential
- *     part kept) with total internal reflection, no Fresnel weights;
+ *     part kept) with total internal reflection; Fresnel weights are an option
+ *     (OR_FLAG_FRESNEL: unpolarised reflectance, one reflected branch per
+ *     crossing of a not yet reflected path, at most OR_MAX_BRANCHES per
+ *     sample, branches not split again);
+ *   - the referenced cloak (Figs. 5-7) divides the index inside the box by
+ *     n_min = 1/(1 + kA); its ideal reference is a homogeneous plate of index
+ *     1 + kA filling the box from the flat mirror (y = 0) to the box top;
  *   - the photograph (Fig. 2a) is replaced by a synthetic background plane.
  *
  * Parity unpinned: 3-D rays (p_z != 0) and total internal reflection at the
@@ -62,7 +68,23 @@ typedef struct or_scene {
     int32_t background;               /* 0 checkerboard, 1 texture                           */
     int32_t tex_size, integrator;     /* integrator: 0 RK4 fixed step, 1 Dormand-Prince 5(4) */
     int32_t max_bounces;
+    int32_t flags;                    /* OR_FLAG_* below                                      */
 } or_scene;
+
+/* Options of Sec. 3 and Figs. 5-7:
+   REFERENCED  the cloak's index profile divided by n_min = 1/(1 + kA), so that
+               it is >= 1; the air keeps n = 1 (Sec. 4, Figs. 5-7);
+   PLATE       no cloak: a homogeneous dielectric plate of index 1/n_min on the
+               flat mirror, filling the cloak's box from the mirror (y = 0) to
+               the box top (the "ideal" references of Figs. 5-7 (a));
+   FRESNEL     Fresnel weights at the box faces (Sec. 3): a crossing keeps the
+               unpolarised transmittance T = 1 - R on the refracted ray, and a
+               ray that has not been Fresnel-reflected yet also starts a branch
+               along the reflected direction with weight R; branches are not
+               split again (rays reflected more than once are neglected).
+               Total internal reflection keeps the full weight. */
+enum { OR_FLAG_REFERENCED = 1, OR_FLAG_PLATE = 2, OR_FLAG_FRESNEL = 4 };
+#define OR_MAX_BRANCHES 8          /* Fresnel branches followed per camera sample */
 
 typedef struct or_record {
     double pos[3], dir[3], rgb[3];
@@ -74,7 +96,7 @@ typedef struct or_record {
 
 enum { ST_OK = 0, ST_SKY = 1, ST_MAX_BOUNCES = 2, ST_MAX_STEPS = 3, ST_NAN = 4 };
 enum { EV_NONE = -1, EV_GRATING = 0, EV_TOP = 1, EV_XP = 2, EV_XM = 3, EV_ZP = 4, EV_ZM = 5, EV_COUNT = 6 };
-enum { MED_AIR = 0, MED_BOX = 1 };
+enum { MED_AIR = 0, MED_BOX = 1, MED_PLATE = 2 };
 
 typedef struct counters { int64_t halley, evals; } counters;
 
@@ -140,6 +162,29 @@ static void or_medium(const or_scene* sc, double x, double y, double complex* W,
     gn[0] = (2.0 * re1 * imw / (m * m) - imw) * k / (m * m * m);
     gn[1] = ((imw * imw - re1 * re1) / (m * m) + re1) * k / (m * m * m);
     gn[2] = 0.0;
+    if (sc->flags & OR_FLAG_REFERENCED) {         /* n / n_min with n_min = 1 / (1 + kA) */
+        const double sidx = 1.0 + k * sc->A;
+        *n *= sidx;
+        gn[0] *= sidx;
+        gn[1] *= sidx;
+    }
+}
+
+/* Index of the homogeneous plate: 1/n_min of the grating cloak, 1 + kA. */
+static double or_plate_index(const or_scene* sc) { return 1.0 + 2.0 * OR_PI * sc->A / sc->Lambda; }
+
+/* Unpolarised Fresnel reflectance R = (rs^2 + rp^2)/2 for a ray going from
+   index n1 into index n2, from the normal components of its momentum on both
+   sides (|p| = n, so n1 cos(theta_1) = |pn1| and n2 cos(theta_2) = |pn2|):
+     rs = (n1 cos1 - n2 cos2) / (n1 cos1 + n2 cos2),
+     rp = (n2 cos1 - n1 cos2) / (n2 cos1 + n1 cos2)
+        = (n2^2 |pn1| - n1^2 |pn2|) / (n2^2 |pn1| + n1^2 |pn2|). */
+static double or_fresnel_R(double n1, double n2, double pn1, double pn2)
+{
+    const double a = fabs(pn1), b = fabs(pn2);
+    const double rs = (a - b) / (a + b);
+    const double rp = (n2 * n2 * a - n1 * n1 * b) / (n2 * n2 * a + n1 * n1 * b);
+    return 0.5 * (rs * rs + rp * rp);
 }
 
 /* Right-hand side in the Hamiltonian parameter: dr/dtau = p, dp/dtau = n grad n.
@@ -386,6 +431,7 @@ static void or_box(const or_scene* sc, double lo[3], double hi[3])
     lo[0] = -0.5 * sc->E; hi[0] = 0.5 * sc->E;
     lo[1] = -sc->A;       hi[1] = -sc->A + sc->H;
     lo[2] = -0.5 * sc->E; hi[2] = 0.5 * sc->E;
+    if (sc->flags & OR_FLAG_PLATE) lo[1] = 0.0;   /* the plate lies on the flat mirror */
 }
 
 /* Entry of the line X + t p (t > 0) into the box by the slab method; returns
@@ -650,17 +696,47 @@ static int or_finite6(const double s[6])
     return 1;
 }
 
-/* Trace from position X with momentum p in the given medium.  In air p is the
-   unit direction; in the box |p| = n.  `surface` names the surface the ray
-   starts on (EV_NONE, EV_GRATING or a face), whose zero at the start is divided
-   out when looking for the next hit. */
-static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], const double p0[3],
-                     int medium, int surface, or_record* rec, traj_buf* tb)
+/* A Fresnel branch waiting to be traced: where it starts, its momentum, its
+   weight and the counters of the path it split from. */
+typedef struct or_branch {
+    double X[3], p[3], w;
+    int medium, surface, bounces, events;
+    int64_t steps;
+} or_branch;
+
+/* Queue a Fresnel branch (reflected momentum pr at X) if the path may split. */
+static void or_push_branch(or_branch* br, int* nbr, const double X[3], const double pr[3], double w, int medium,
+                           int surface, int bounces, int events, int64_t steps)
+{
+    if (!br || *nbr >= OR_MAX_BRANCHES) return;
+    or_branch* b = &br[(*nbr)++];
+    for (int a = 0; a < 3; ++a) { b->X[a] = X[a]; b->p[a] = pr[a]; }
+    b->w = w;
+    b->medium = medium;
+    b->surface = surface;
+    b->bounces = bounces;
+    b->events = events;
+    b->steps = steps;
+}
+
+/* Trace one path from position X with momentum p in the given medium.  In air
+   p is the unit direction; in the box and the plate |p| = n.  `surface` names
+   the surface the ray starts on (EV_NONE, EV_GRATING or a face), whose zero at
+   the start is divided out when looking for the next hit.  w0 is the path's
+   weight; with br != NULL the path may start Fresnel branches (queued in br).
+   The record gets the path's exit, counters and its own (unweighted) colour;
+   *w_out its final weight. */
+static void or_trace_path(const or_scene* sc, const camera* cam, const double X0[3], const double p0[3],
+                          int medium, int surface, double w0, int bounces0, int events0, int64_t steps0,
+                          or_branch* br, int* nbr, or_record* rec, double* w_out, traj_buf* tb)
 {
     double X[3] = {X0[0], X0[1], X0[2]}, p[3] = {p0[0], p0[1], p0[2]};
     counters cnt = {0, 0};
-    int64_t steps = 0;
-    int bounces = 0, events = 0, status = ST_OK;
+    int64_t steps = steps0;
+    int bounces = bounces0, events = events0, status = ST_OK;
+    double w = w0;
+    const int fresnel = (sc->flags & OR_FLAG_FRESNEL) != 0;
+    const int plate = (sc->flags & OR_FLAG_PLATE) != 0;
     double rgb[3] = {0.0, 0.0, 0.0};
     for (;;) {
         if (bounces > sc->max_bounces) { status = ST_MAX_BOUNCES; break; }
@@ -668,14 +744,19 @@ static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], 
             double t_m = sc->mirror ? or_trochoid_line_hit(sc, X, p, surface == EV_GRATING)
                                     : or_flat_line_hit(X, p);
             int face = EV_NONE;
-            double t_b = sc->cloak ? or_box_entry(sc, X, p, &face) : INFINITY;
+            double t_b = (sc->cloak || plate) ? or_box_entry(sc, X, p, &face) : INFINITY;
             if (t_b < t_m) {
                 for (int a = 0; a < 3; ++a) X[a] += t_b * p[a];
                 double Nf[3];
                 or_face_normal(face, Nf);              /* outward normal of the entry face */
-                double complex W;
-                double n, gn[3];
-                or_medium(sc, X[0], X[1], &W, &n, gn, &cnt);
+                double n;
+                if (plate) {
+                    n = or_plate_index(sc);
+                } else {
+                    double complex W;
+                    double gn[3];
+                    or_medium(sc, X[0], X[1], &W, &n, gn, &cnt);
+                }
                 const double pn = or_dot(p, Nf);
                 double pt[3];
                 for (int a = 0; a < 3; ++a) pt[a] = p[a] - pn * Nf[a];
@@ -687,8 +768,15 @@ static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], 
                     continue;
                 }
                 const double pn_in = sqrt(n * n - pt2);
+                if (fresnel) {
+                    const double R = or_fresnel_R(1.0, n, pn, pn_in);
+                    double pr[3];
+                    for (int a = 0; a < 3; ++a) pr[a] = p[a] - 2.0 * pn * Nf[a];
+                    or_push_branch(br, nbr, X, pr, w * R, MED_AIR, EV_NONE, bounces, events, steps);
+                    w *= 1.0 - R;
+                }
                 for (int a = 0; a < 3; ++a) p[a] = pt[a] - pn_in * Nf[a];
-                medium = MED_BOX;
+                medium = plate ? MED_PLATE : MED_BOX;
                 surface = face;
                 continue;
             }
@@ -704,6 +792,58 @@ static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], 
             }
             status = or_background(sc, cam, X, p, rgb);
             break;
+        }
+
+        if (medium == MED_PLATE) {
+            /* Inside the homogeneous plate: a straight segment to the mirror
+               (y = 0), the top or a side face. */
+            double lo[3], hi[3];
+            or_box(sc, lo, hi);
+            double tmin = INFINITY;
+            int hit = EV_NONE;
+            for (int a = 0; a < 3; ++a) {
+                if (p[a] == 0.0) continue;
+                const double t = ((p[a] > 0.0 ? hi[a] : lo[a]) - X[a]) / p[a];
+                int f;
+                if (a == 0) f = p[a] > 0.0 ? EV_XP : EV_XM;
+                else if (a == 1) f = p[a] > 0.0 ? EV_TOP : EV_GRATING;   /* EV_GRATING: the mirror */
+                else f = p[a] > 0.0 ? EV_ZP : EV_ZM;
+                if (t < tmin) { tmin = t; hit = f; }
+            }
+            if (!(tmin < INFINITY) || hit == EV_NONE) { status = ST_NAN; break; }
+            if (tmin < 0.0) tmin = 0.0;
+            for (int a = 0; a < 3; ++a) X[a] += tmin * p[a];
+            if (hit == EV_GRATING) {
+                X[1] = 0.0;
+                p[1] = -p[1];
+                bounces++;
+                surface = EV_GRATING;
+                continue;
+            }
+            double Nf[3];
+            or_face_normal(hit, Nf);
+            const double pn = or_dot(p, Nf);
+            double pt[3];
+            for (int a = 0; a < 3; ++a) pt[a] = p[a] - pn * Nf[a];
+            const double pt2 = or_dot(pt, pt);
+            if (pt2 >= 1.0) {                           /* total internal reflection */
+                for (int a = 0; a < 3; ++a) p[a] -= 2.0 * pn * Nf[a];
+                bounces++;
+                surface = hit;
+                continue;
+            }
+            const double pn_out = sqrt(1.0 - pt2);
+            if (fresnel) {
+                const double R = or_fresnel_R(or_plate_index(sc), 1.0, pn, pn_out);
+                double pr[3];
+                for (int a = 0; a < 3; ++a) pr[a] = p[a] - 2.0 * pn * Nf[a];
+                or_push_branch(br, nbr, X, pr, w * R, MED_PLATE, hit, bounces, events, steps);
+                w *= 1.0 - R;
+            }
+            for (int a = 0; a < 3; ++a) p[a] = pt[a] + pn_out * Nf[a];
+            medium = MED_AIR;
+            surface = EV_NONE;
+            continue;
         }
 
         /* Inside the cloak: integrate the ray ODE step by step. */
@@ -805,6 +945,14 @@ static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], 
                 continue;
             }
             const double pn_out = sqrt(1.0 - pt2);
+            if (fresnel) {
+                const double n1 = sqrt(s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);   /* |p| = n */
+                const double R = or_fresnel_R(n1, 1.0, pn, pn_out);
+                double pr[3];
+                for (int a = 0; a < 3; ++a) pr[a] = s[3 + a] - 2.0 * pn * Nf[a];
+                or_push_branch(br, nbr, s, pr, w * R, MED_BOX, ev_best, bounces, events, steps);
+                w *= 1.0 - R;
+            }
             for (int a = 0; a < 3; ++a) { X[a] = s[a]; p[a] = pt[a] + pn_out * Nf[a]; }
             medium = MED_AIR;
             surface = EV_NONE;
@@ -835,6 +983,34 @@ static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], 
         rec->events = events;
         rec->pad = 0;
     }
+    if (w_out) *w_out = w;
+}
+
+/* One camera sample: the path from (X0, p0) and, with Fresnel weights, the
+   branches it started, traced in the order they were started.  The record is
+   the first path's; its colour is the weighted sum over the paths. */
+static void or_trace(const or_scene* sc, const camera* cam, const double X0[3], const double p0[3],
+                     int medium, int surface, or_record* rec, traj_buf* tb)
+{
+    or_record local;
+    if (!rec) rec = &local;
+    if (!(sc->flags & OR_FLAG_FRESNEL)) {
+        or_trace_path(sc, cam, X0, p0, medium, surface, 1.0, 0, 0, 0, NULL, NULL, rec, NULL, tb);
+        return;
+    }
+    or_branch br[OR_MAX_BRANCHES];
+    int nbr = 0;
+    double w = 0.0;
+    or_trace_path(sc, cam, X0, p0, medium, surface, 1.0, 0, 0, 0, br, &nbr, rec, &w, tb);
+    double acc[3] = {w * rec->rgb[0], w * rec->rgb[1], w * rec->rgb[2]};
+    for (int q = 0; q < nbr; ++q) {
+        or_record r;
+        double wq = 0.0;
+        or_trace_path(sc, cam, br[q].X, br[q].p, br[q].medium, br[q].surface, br[q].w, br[q].bounces,
+                      br[q].events, br[q].steps, NULL, NULL, &r, &wq, NULL);
+        for (int a = 0; a < 3; ++a) acc[a] += wq * r.rgb[a];
+    }
+    for (int a = 0; a < 3; ++a) rec->rgb[a] = acc[a];
 }
 
 /* ------------------------------------------------------------------------ */
@@ -919,7 +1095,39 @@ uint64_t or_splitmix64_out(uint64_t seed, uint64_t m) { return or_splitmix64(see
 static int or_scene_ok(const or_scene* sc)
 {
     if (sc->background == 1 && (!sc->tex || sc->tex_size <= 0)) return 0;
+    if ((sc->flags & OR_FLAG_PLATE) && (sc->cloak || sc->mirror)) return 0;   /* the plate lies on the flat mirror */
     return 1;
+}
+
+/* Unpolarised Fresnel reflectance from index n1 into index n2 at incidence
+   cosine cos_i; 1 beyond the critical angle. */
+double or_fresnel(double n1, double n2, double cos_i)
+{
+    const double sin2 = 1.0 - cos_i * cos_i;
+    const double c2 = n2 * n2 - n1 * n1 * sin2;
+    if (c2 <= 0.0) return 1.0;
+    return or_fresnel_R(n1, n2, n1 * cos_i, sqrt(c2));
+}
+
+/* Every path of one sample started at (X, p): the first path's record and
+   weight, then each Fresnel branch's, in the order they were started (at most
+   cap records).  Returns the number of paths in *n. */
+int or_trace_paths(const or_scene* sc, const double* X, const double* p, int32_t medium, int32_t surface,
+                   or_record* recs, double* weights, int32_t cap, int32_t* n)
+{
+    if (!or_scene_ok(sc) || cap < 1) return -1;
+    camera cam;
+    or_camera(sc, &cam);
+    or_branch br[OR_MAX_BRANCHES];
+    int nbr = 0;
+    or_trace_path(sc, &cam, X, p, medium, surface, 1.0, 0, 0, 0,
+                  (sc->flags & OR_FLAG_FRESNEL) ? br : NULL, &nbr, &recs[0], &weights[0], NULL);
+    int k = 1;
+    for (int q = 0; q < nbr && k < cap; ++q, ++k)
+        or_trace_path(sc, &cam, br[q].X, br[q].p, br[q].medium, br[q].surface, br[q].w, br[q].bounces,
+                      br[q].events, br[q].steps, NULL, NULL, &recs[k], &weights[k], NULL);
+    *n = k;
+    return 0;
 }
 
 int or_trace_from(const or_scene* sc, const double* X, const double* p, int32_t medium, int32_t surface,

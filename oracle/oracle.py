@@ -45,7 +45,7 @@ class OrScene(C.Structure):
         ("width", C.c_int32), ("height", C.c_int32), ("spp", C.c_int32), ("centre_line", C.c_int32),
         ("background", C.c_int32),
         ("tex_size", C.c_int32), ("integrator", C.c_int32),
-        ("max_bounces", C.c_int32),
+        ("max_bounces", C.c_int32), ("flags", C.c_int32),
     ]
 
 
@@ -93,6 +93,10 @@ def lib():
         L.or_fov_columns.argtypes = [C.c_int32, C.c_double, C.c_double, C.POINTER(C.c_int32),
                                      C.POINTER(C.c_int32)]
         L.or_max_threads.restype = C.c_int
+        L.or_fresnel.argtypes = [C.c_double, C.c_double, C.c_double]
+        L.or_fresnel.restype = C.c_double
+        L.or_trace_paths.argtypes = [C.POINTER(OrScene), dp, dp, C.c_int32, C.c_int32, C.c_void_p, dp, C.c_int32,
+                                     C.POINTER(C.c_int32)]
         _lib = L
     return _lib
 
@@ -188,6 +192,27 @@ def trace_from(sc: Scene, X, p, medium: int = 0, surface: int = -1, traj_cap: in
     return rec[0], traj[: n.value]
 
 
+FLAG_REFERENCED, FLAG_PLATE, FLAG_FRESNEL = 1, 2, 4
+
+
+def fresnel(n1: float, n2: float, cos_i: float) -> float:
+    """Unpolarised Fresnel reflectance from index n1 into n2 at incidence cosine cos_i."""
+    return float(lib().or_fresnel(n1, n2, cos_i))
+
+
+def trace_paths(sc: Scene, X, p, medium: int = 0, surface: int = -1, cap: int = 9):
+    """Records and weights of every path of one sample: the first path, then
+    its Fresnel branches in the order they were started."""
+    X = np.ascontiguousarray(np.asarray(X, float))
+    p = np.ascontiguousarray(np.asarray(p, float))
+    rec = np.zeros(cap, dtype=RECORD_DTYPE)
+    w = np.zeros(cap)
+    n = C.c_int32(0)
+    if lib().or_trace_paths(sc.ref, _dp(X), _dp(p), medium, surface, rec.ctypes.data, _dp(w), cap, C.byref(n)):
+        raise ValueError("oracle: invalid scene")
+    return rec[: n.value], w[: n.value]
+
+
 def render_pixels(sc: Scene, pix, nthreads: int = 0, records: bool = False):
     pix = np.ascontiguousarray(np.asarray(pix, dtype=np.int64))
     rgb = np.zeros((pix.size, 3), dtype=np.float32)
@@ -195,7 +220,8 @@ def render_pixels(sc: Scene, pix, nthreads: int = 0, records: bool = False):
     if lib().or_render_pixels(sc.ref, pix.ctypes.data_as(C.POINTER(C.c_int64)), pix.size,
                               rgb.ctypes.data_as(C.POINTER(C.c_float)),
                               rec.ctypes.data if records else None, nthreads):
-        raise ValueError("oracle: texture background without a texture")
+        raise ValueError("oracle: invalid scene (texture background without a texture, or a plate "
+                         "without the flat mirror alone)")
     return (rgb, rec) if records else rgb
 
 

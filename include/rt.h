@@ -71,6 +71,27 @@ extern "C" {
 #define RT_RAY_MAX_STEPS 3    /* more than max_steps integrator steps          */
 #define RT_RAY_NAN 4          /* non-finite state                              */
 
+/* rt_scene_desc.flags (Sec. 3, Sec. 4 and Figs. 5-7):
+   RT_FLAG_REFERENCED  the cloak's index divided by n_min = 1/(1 + kA), so it is
+                       >= 1 everywhere; the air keeps n = 1
+   RT_FLAG_PLATE       no cloak: a homogeneous dielectric plate of index
+                       1/n_min = 1 + kA on the flat mirror, filling the cloak's
+                       box from the mirror (y = 0) to the box top (the ideal
+                       reference of the referenced cloak); needs
+                       mirror = RT_MIRROR_FLAT and cloak = 0
+   RT_FLAG_FRESNEL     Fresnel weights at the box faces: a crossing keeps the
+                       unpolarised transmittance on the refracted ray, and the
+                       camera's path also traces each reflected ray (weight R,
+                       at most 8 per sample), which is not split again (rays
+                       Fresnel-reflected more than once are neglected); total
+                       internal reflection keeps the full weight.
+   Scenes with any of these are rendered by the wavefront loop (launch
+   variant 3) only, in a build of it that the scenes without options do not
+   pay for. */
+#define RT_FLAG_REFERENCED 1
+#define RT_FLAG_PLATE 2
+#define RT_FLAG_FRESNEL 4
+
 /*
  * Scene descriptor.  The camera is a pinhole at distance cam_dist from the
  * origin at elevation elev_deg and azimuth azim_deg, looking at the origin,
@@ -107,7 +128,7 @@ typedef struct rt_scene_desc {
     int32_t integrator;       /* RT_RK4 | RT_DP45                               */
     int32_t precision;        /* RT_FP32 | RT_FP64                              */
     int32_t max_bounces;      /* guard on reflections per ray                   */
-    int32_t flags;            /* reserved, 0                                    */
+    int32_t flags;            /* RT_FLAG_* (0: the plain method)                */
 } rt_scene_desc;
 
 /* Per-sample exit record: the start of the ray's final straight segment (its

@@ -57,6 +57,8 @@ struct rt_scene {
     float* d_samp;            // wavefront loop: per-sample colours and per-pixel counters,
     int* d_pcnt;              // grown on demand (stream-ordered)
     int64_t samp_cap, pix_cap;
+    void* d_branch;           // Fresnel branch queues of the wavefront loop (stream-ordered)
+    size_t branch_cap;
     cudaEvent_t done;
     bool rendered;
 };
@@ -105,7 +107,11 @@ static int validate(const rt_scene_desc* d)
     if (d->background == RT_BG_CHECKER) RT_REQ(d->bg_cell > 0.0, "bg_cell must be > 0");
     else RT_REQ(d->tex && d->tex_size > 0 && d->tex_texel > 0.0, "texture background needs tex, tex_size, tex_texel");
     RT_REQ(d->max_bounces >= 0 && d->max_steps >= 1, "max_bounces >= 0 and max_steps >= 1");
-    RT_REQ(d->flags == 0, "flags must be 0");
+    RT_REQ((d->flags & ~(RT_FLAG_REFERENCED | RT_FLAG_PLATE | RT_FLAG_FRESNEL)) == 0, "flags: unknown bits");
+    RT_REQ(!(d->flags & RT_FLAG_PLATE) || (d->mirror == RT_MIRROR_FLAT && d->cloak == 0),
+           "flags: the plate lies on the flat mirror (mirror = RT_MIRROR_FLAT, cloak = 0)");
+    RT_REQ(!(d->flags & RT_FLAG_PLATE) || (d->H > d->A && d->E > 0.0 && std::isfinite(d->H) && std::isfinite(d->E)),
+           "the plate needs H > A and E > 0");
     const double wout = d->centre_line ? 1.0 : (double)d->width;
     RT_REQ((double)d->height * wout * (double)d->spp < 4.0e18, "image too large");
     return RT_OK;
@@ -172,6 +178,14 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     // FP32 Newton stop on W0: absolute, scaled by kA (|W| < kA in the cloak)
     s->cf.w0tol = (float)(Mth<float>::kRel * s->kA);
     s->cd.w0tol = Mth<double>::kRel * s->kA;
+    // index scale of the referenced cloak (n / n_min) and the plate's index
+    s->flags = d->flags;
+    s->idx_scale = (d->flags & RT_FLAG_REFERENCED) ? 1.0 + s->kA : 1.0;
+    s->plate_n = 1.0 + s->kA;
+    s->cd.fk = kTwoPi * s->idx_scale * s->idx_scale;
+    s->cf.fk = (float)s->cd.fk;
+    s->cd.ybot = (d->flags & RT_FLAG_PLATE) ? 0.0 : -s->A;
+    s->cf.ybot = (float)s->cd.ybot;
     for (int a = 0; a < 3; ++a) {
         s->ad.fr[a] = s->fr[a]; s->ad.ur[a] = s->ur[a]; s->ad.r[a] = s->r[a]; s->ad.Pb[a] = s->Pb[a];
         s->af.fr[a] = (float)s->fr[a]; s->af.ur[a] = (float)s->ur[a]; s->af.r[a] = (float)s->r[a];
@@ -182,7 +196,7 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->af.inv_cell = (float)s->ad.inv_cell;
     s->af.inv_texel = (float)s->ad.inv_texel;
     s->ymirror = d->mirror == RT_MIRROR_TROCHOID ? s->A : 0.0;
-    s->box_lo[0] = -s->E2; s->box_lo[1] = -s->A; s->box_lo[2] = -s->E2;
+    s->box_lo[0] = -s->E2; s->box_lo[1] = (d->flags & RT_FLAG_PLATE) ? 0.0 : -s->A; s->box_lo[2] = -s->E2;
     s->box_hi[0] = s->E2; s->box_hi[1] = s->ytop; s->box_hi[2] = s->E2;
     s->inv_m = s->m > 0 ? 1.0 / s->m : 0.0;
     s->two_over_w = 2.0 / (double)d->width;
@@ -249,7 +263,7 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     int bps = 0;
     s->variant = kDefaultVariant;
     s->min_active = kMinActive;
-    cudaError_t e = render_occupancy(desc->precision, desc->integrator, s->variant, &bps);
+    cudaError_t e = render_occupancy(desc->precision, desc->integrator, s->variant, desc->flags != 0, &bps);
     int nsm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     s->nsm = nsm;
@@ -282,6 +296,7 @@ void rt_destroy_scene(rt_scene* s)
     if (s->d_host_rgb8) cudaFree(s->d_host_rgb8);
     if (s->d_samp) cudaFree(s->d_samp);
     if (s->d_pcnt) cudaFree(s->d_pcnt);
+    if (s->d_branch) cudaFree(s->d_branch);
     if (s->done) cudaEventDestroy(s->done);
     free(s);
 }
@@ -300,7 +315,21 @@ static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float
     sc.pix_list = d_pix;
     sc.nwork = nwork;
     RT_CK(cudaMemsetAsync(s->d_counters, 0, kCounters * sizeof(unsigned long long), st));
-    SampleScratch ss = {nullptr, nullptr};
+    RT_REQ(s->desc.flags == 0 || s->variant == kVariantWave,
+           "scene options (RT_FLAG_*) are rendered by the wavefront loop (variant %d) only", kVariantWave);
+    SampleScratch ss = {nullptr, nullptr, nullptr};
+    if (nwork > 0 && (s->desc.flags & RT_FLAG_FRESNEL)) {
+        const size_t bytes = branch_queue_bytes(s->desc.precision, s->grid);
+        if (bytes > s->branch_cap) {
+            RT_CK(cudaStreamWaitEvent(st, s->done, 0));
+            if (s->d_branch) RT_CK(cudaFreeAsync(s->d_branch, st));
+            s->d_branch = nullptr;
+            s->branch_cap = 0;
+            RT_CK(cudaMallocAsync(&s->d_branch, bytes, st));
+            s->branch_cap = bytes;
+        }
+        ss.br = s->d_branch;
+    }
     if (nwork > 0 && s->variant == kVariantWave && sc.spp > 1) {
         // the wavefront loop traces the samples of a pixel at the same time
         const int64_t ns = nwork * sc.spp;
@@ -388,7 +417,7 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
     // cloak and the power of two of the number of samples
     const double samples = (double)s->dev.nwork * d.spp;
     char key[160];
-    snprintf(key, sizeof key, "scene/p%d/i%d/c%d/m%d/log2n%d", d.precision, d.integrator, d.cloak, d.mirror,
+    snprintf(key, sizeof key, "scene/p%d/i%d/c%d/m%d/f%d/log2n%d", d.precision, d.integrator, d.cloak, d.mirror, d.flags,
              (int)floor(log2(samples > 1.0 ? samples : 1.0)));
     int v = kDefaultVariant, m = kMinActive;
     if (!tune_lookup(key, &v, &m)) {
@@ -401,6 +430,7 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
         int rc = RT_OK;
         for (int var = 0; var < kVariants && rc == RT_OK; ++var) {
             if (!variant_compiled(d.precision, d.integrator, var)) continue;
+            if (d.flags != 0 && var != kVariantWave) continue;
             for (int c : cand) {
                 rc = rt_scene_set_launch(s, var, c);
                 if (rc != RT_OK) break;
@@ -437,10 +467,12 @@ int rt_scene_set_launch(rt_scene* s, int32_t variant, int32_t min_active)
     RT_REQ(variant >= -1 && variant < kVariants, "variant must be -1 (keep) or 0..%d", kVariants - 1);
     RT_REQ(variant < 0 || variant_compiled(s->desc.precision, s->desc.integrator, variant),
            "variant %d is not compiled for this precision and integrator", variant);
+    RT_REQ(variant < 0 || variant == kVariantWave || s->desc.flags == 0,
+           "scene options (RT_FLAG_*) are rendered by the wavefront loop (variant %d) only", kVariantWave);
     RT_REQ(min_active == 0 || (min_active >= 1 && min_active <= 32), "min_active must be 0 (keep) or 1..32");
     if (variant >= 0 && variant != s->variant) {
         int bps = 0;
-        RT_CK(render_occupancy(s->desc.precision, s->desc.integrator, variant, &bps));
+        RT_CK(render_occupancy(s->desc.precision, s->desc.integrator, variant, s->desc.flags != 0, &bps));
         RT_REQ(bps > 0, "variant %d does not fit on this device", variant);
         s->variant = variant;
         s->grid = bps * s->nsm;

@@ -18,7 +18,7 @@ namespace grt {
 
 // Many scenes in one launch of the wavefront loop: their samples form one
 // work list, so the warps balance across scenes of uneven size.
-template <class R, int INTEG>
+template <class R, int INTEG, bool OPT>
 static cudaError_t batch_prepare()
 {
     static std::atomic<unsigned long long> done{0};
@@ -27,44 +27,62 @@ static cudaError_t batch_prepare()
     if (e != cudaSuccess) return e;
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return cudaSuccess;
-    e = cudaFuncSetAttribute(wave_batch_kernel<R, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    e = cudaFuncSetAttribute(wave_batch_kernel<R, INTEG, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)wave_smem_bytes<R>());
     if (e == cudaSuccess) done.fetch_or(bit);
     return e;
 }
 
-template <class R, int INTEG>
+template <class R, int INTEG, bool OPT>
 static cudaError_t batch_occupancy_t(int* bps)
 {
-    const cudaError_t e = batch_prepare<R, INTEG>();
+    const cudaError_t e = batch_prepare<R, INTEG, OPT>();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_batch_kernel<R, INTEG>, kWaveBlock,
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_batch_kernel<R, INTEG, OPT>, kWaveBlock,
                                                          wave_smem_bytes<R>());
 }
 
-cudaError_t batch_occupancy(int precision, int integrator, int* bps)
+template <bool OPT>
+static cudaError_t batch_occupancy_o(int precision, int integrator, int* bps)
 {
     if (precision == RT_FP64)
-        return integrator == RT_DP45 ? batch_occupancy_t<double, RT_DP45>(bps) : batch_occupancy_t<double, RT_RK4>(bps);
-    return integrator == RT_DP45 ? batch_occupancy_t<float, RT_DP45>(bps) : batch_occupancy_t<float, RT_RK4>(bps);
+        return integrator == RT_DP45 ? batch_occupancy_t<double, RT_DP45, OPT>(bps)
+                                     : batch_occupancy_t<double, RT_RK4, OPT>(bps);
+    return integrator == RT_DP45 ? batch_occupancy_t<float, RT_DP45, OPT>(bps)
+                                 : batch_occupancy_t<float, RT_RK4, OPT>(bps);
 }
 
-template <class R, int INTEG>
+cudaError_t batch_occupancy(int precision, int integrator, bool opt, int* bps)
+{
+    return opt ? batch_occupancy_o<true>(precision, integrator, bps)
+               : batch_occupancy_o<false>(precision, integrator, bps);
+}
+
+template <class R, int INTEG, bool OPT>
 static cudaError_t launch_batch_t(const BatchLaunch& L, cudaStream_t stream)
 {
-    const cudaError_t e = batch_prepare<R, INTEG>();
+    const cudaError_t e = batch_prepare<R, INTEG, OPT>();
     if (e != cudaSuccess) return e;
-    wave_batch_kernel<R, INTEG><<<L.grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+    wave_batch_kernel<R, INTEG, OPT><<<L.grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
         L.scenes, L.offsets, L.soffsets, L.rgbs, L.n, L.total, L.total_samples, L.scratch.col, L.scratch.cnt,
-        L.counters, L.min_active);
+        L.scratch.br, L.counters, L.min_active);
     return cudaGetLastError();
+}
+
+template <bool OPT>
+static cudaError_t launch_batch_o(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream)
+{
+    if (precision == RT_FP64)
+        return integrator == RT_DP45 ? launch_batch_t<double, RT_DP45, OPT>(L, stream)
+                                     : launch_batch_t<double, RT_RK4, OPT>(L, stream);
+    return integrator == RT_DP45 ? launch_batch_t<float, RT_DP45, OPT>(L, stream)
+                                 : launch_batch_t<float, RT_RK4, OPT>(L, stream);
 }
 
 cudaError_t launch_batch(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream)
 {
-    if (precision == RT_FP64)
-        return integrator == RT_DP45 ? launch_batch_t<double, RT_DP45>(L, stream) : launch_batch_t<double, RT_RK4>(L, stream);
-    return integrator == RT_DP45 ? launch_batch_t<float, RT_DP45>(L, stream) : launch_batch_t<float, RT_RK4>(L, stream);
+    return L.opt ? launch_batch_o<true>(precision, integrator, L, stream)
+                 : launch_batch_o<false>(precision, integrator, L, stream);
 }
 
 // ------------------------------------------------------------------------
@@ -148,6 +166,8 @@ struct rt_batch {
     int64_t* d_soffsets;     // first sample of each scene
     float* d_samp;           // per-sample colours of multi-sample pixels
     int* d_pcnt;             // per-pixel sample counters
+    void* d_br;              // Fresnel branch queues (when a scene has RT_FLAG_FRESNEL)
+    bool opt;                // a scene has options (RT_FLAG_*): the options build of the loop
     float** d_rgbs;
     std::vector<float*> h_rgbs;        // output pointers last uploaded
     unsigned long long* d_counters;
@@ -167,6 +187,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     std::vector<DevScene> dev(n);
     std::vector<int64_t> off(n + 1, 0), soff(n + 1, 0);
     int precision = -1, integrator = -1, device = -1;
+    bool fresnel = false, opt = false;
     for (int i = 0; i < n; ++i) {
         RT_REQ(scenes[i], "scene %d is NULL", i);
         int p, g, d;
@@ -177,6 +198,8 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
         RT_REQ(d == device, "scenes of a batch must live on one device (scene %d)", i);
         off[i + 1] = off[i] + dev[i].nwork;
         soff[i + 1] = soff[i] + dev[i].nwork * dev[i].spp;
+        fresnel = fresnel || (dev[i].flags & RT_FLAG_FRESNEL);
+        opt = opt || dev[i].flags != 0;
     }
     int cur = -1;
     RT_CK(cudaGetDevice(&cur));
@@ -206,7 +229,8 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     if (e == cudaSuccess) e = cudaMemset(b->d_counters, 0, sizeof(unsigned long long) * kCounters);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     int bps = 0;
-    if (e == cudaSuccess) e = batch_occupancy(precision, integrator, &bps);
+    b->opt = opt;
+    if (e == cudaSuccess) e = batch_occupancy(precision, integrator, opt, &bps);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
         set_error("rt_batch_create: %s", cudaGetErrorString(e));
@@ -214,6 +238,14 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
         return e == cudaErrorMemoryAllocation ? RT_ENOMEM : RT_ECUDA;
     }
     b->grid = (bps > 0 ? bps : 1) * b->nsm;
+    if (fresnel) {
+        e = cudaMalloc(&b->d_br, branch_queue_bytes(precision, b->grid));
+        if (e != cudaSuccess) {
+            set_error("rt_batch_create: %s", cudaGetErrorString(e));
+            rt_batch_destroy(b);
+            return RT_ENOMEM;
+        }
+    }
     *out = b;
     return RT_OK;
 }
@@ -229,6 +261,7 @@ void rt_batch_destroy(rt_batch* b)
     if (b->d_soffsets) cudaFree(b->d_soffsets);
     if (b->d_samp) cudaFree(b->d_samp);
     if (b->d_pcnt) cudaFree(b->d_pcnt);
+    if (b->d_br) cudaFree(b->d_br);
     if (b->d_rgbs) cudaFree(b->d_rgbs);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->done) cudaEventDestroy(b->done);
@@ -258,7 +291,8 @@ int rt_batch_render(rt_batch* b, float* const* d_rgb, void* stream)
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_counters, 0, sizeof(unsigned long long) * kCounters, cap);
         if (e == cudaSuccess) e = cudaMemsetAsync(b->d_pcnt, 0, kScratchBytesPerPixel * (size_t)b->total, cap);
         const BatchLaunch L = {b->d_scenes, b->d_offsets, b->d_soffsets, b->d_rgbs, b->n, b->total,
-                               b->total_samples, {b->d_samp, b->d_pcnt}, b->d_counters, b->min_active, b->grid};
+                               b->total_samples, {b->d_samp, b->d_pcnt, b->d_br}, b->d_counters, b->min_active,
+                               b->grid, b->opt};
         if (e == cudaSuccess) e = launch_batch(b->precision, b->integrator, L, cap);
         cudaGraph_t g = nullptr;
         const cudaError_t e2 = cudaStreamEndCapture(cap, &g);

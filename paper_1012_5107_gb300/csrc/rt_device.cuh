@@ -28,6 +28,8 @@ struct StepConst {
     R kA, A, h, ytop, E2;
     R rtol, atol, hmax;
     R w0tol;     // FP32: Newton on W0 stops when |dW|^2 <= w0tol
+    R fk;        // force factor k s^2 (s: index scale of the cloak, 1 unless referenced)
+    R ybot;      // bottom of the box: -A (cloak) or 0 (plate on the flat mirror)
 };
 
 // Constants of the straight segments to the background, in the path's precision.
@@ -60,6 +62,9 @@ struct DevScene {
     int64_t nwork;                          // pixels to render
     int mirror, cloak, width, height, wout, spp, m, centre_line;
     int background, tex_size, integrator, max_bounces;
+    int flags;                              // RT_FLAG_*
+    double idx_scale;                       // index scale inside the cloak (1 + kA when referenced)
+    double plate_n;                         // index of the dielectric plate (1 + kA)
 };
 
 // ------------------------------------------------------------------------
@@ -198,14 +203,16 @@ __device__ __forceinline__ void w0_predict(R& wr, R& wi, R rr, R ri, R dx, R dy)
 }
 
 // Ray force F = grad(n^2)/2 = n grad n (Eq. 12 times n) in the Hamiltonian
-// parameter: F = k n^2 (Im(W r^2), Re(W r^2)) with r = 1/(1+W), n^2 = |r|^2.
+// parameter: F = k n^2 (Im(W r^2), Re(W r^2)) with r = 1/(1+W), n^2 = |r|^2;
+// an index scaled by s inside the cloak (the referenced cloak, n / n_min)
+// scales the force by s^2: fk = k s^2.
 template <class R>
-__device__ __forceinline__ void ray_force(R wr, R wi, R rr, R ri, R& Fx, R& Fy)
+__device__ __forceinline__ void ray_force(R wr, R wi, R rr, R ri, R fk, R& Fx, R& Fy)
 {
     const R n2 = rr * rr + ri * ri;
     const R r2r = rr * rr - ri * ri, r2i = R(2) * rr * ri;
     const R gr = wr * r2r - wi * r2i, gi = wr * r2i + wi * r2r;
-    const R s = R(kTwoPi) * n2;
+    const R s = fk * n2;
     Fx = s * gi;
     Fy = s * gr;
 }

@@ -33,13 +33,17 @@ struct Windows {
 
 // Whether launch variant `variant` exists for this precision and integrator.
 bool variant_compiled(int precision, int integrator, int variant);
-cudaError_t render_occupancy(int precision, int integrator, int variant, int* blocks_per_sm);
+// opt: the options build of the wavefront loop (scenes with RT_FLAG_* set)
+cudaError_t render_occupancy(int precision, int integrator, int variant, bool opt, int* blocks_per_sm);
 // Scratch of the wavefront loop for pixels of several samples: 3 floats per
 // sample (col) and one counter per pixel (cnt, zero at launch).
 struct SampleScratch {
     float* col;
     int* cnt;
+    void* br;        // Fresnel branch queues (RT_FLAG_FRESNEL), see wave_branch_bytes
 };
+// Bytes of the Fresnel branch queues a wavefront launch of `grid` blocks needs.
+size_t branch_queue_bytes(int precision, int grid);
 constexpr size_t kScratchBytesPerSample = 3 * sizeof(float);
 constexpr size_t kScratchBytesPerPixel = sizeof(int);
 
@@ -77,7 +81,7 @@ namespace grt {
 bool tune_lookup(const std::string& key, int* variant, int* min_active);
 // Scene table of a validated descriptor (texture pointer left to the caller).
 void build_scene_table(const rt_scene_desc* d, DevScene* s);
-cudaError_t batch_occupancy(int precision, int integrator, int* bps);
+cudaError_t batch_occupancy(int precision, int integrator, bool opt, int* bps);
 // One launch of the wavefront loop over the pixels of n scenes (device tables).
 struct BatchLaunch {
     const DevScene* scenes;
@@ -89,6 +93,7 @@ struct BatchLaunch {
     SampleScratch scratch;       // for total_samples samples and total pixels
     unsigned long long* counters;
     int min_active, grid;
+    bool opt;                    // a scene has options (RT_FLAG_*): the options build
 };
 cudaError_t launch_batch(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream);
 void tune_record(const std::string& key, int variant, int min_active);

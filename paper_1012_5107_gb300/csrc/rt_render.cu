@@ -21,23 +21,29 @@ static cudaError_t allow_smem(K kernel, size_t bytes, std::atomic<unsigned long 
     return e;
 }
 
-template <class R, int INTEG>
+template <class R, int INTEG, bool OPT>
 static cudaError_t wave_prepare()
 {
     static std::atomic<unsigned long long> done{0};
-    return allow_smem(wave_kernel<R, INTEG>, wave_smem_bytes<R>(), done);
+    return allow_smem(wave_kernel<R, INTEG, OPT>, wave_smem_bytes<R>(), done);
 }
 
 // Register-budget variants of the per-lane loop are compiled for the FP32 RK4
 // kernel, the one the benchmark times; the other (precision, integrator)
 // pairs have one each.  Every pair has the wavefront loop.
 template <class R, int INTEG>
-static cudaError_t occupancy_t(int variant, int* bps)
+static cudaError_t occupancy_t(int variant, bool opt, int* bps)
 {
     if (variant == kVariantWave) {
-        const cudaError_t e = wave_prepare<R, INTEG>();
+        if (opt) {
+            const cudaError_t e = wave_prepare<R, INTEG, true>();
+            if (e != cudaSuccess) return e;
+            return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, true>, kWaveBlock,
+                                                                 wave_smem_bytes<R>());
+        }
+        const cudaError_t e = wave_prepare<R, INTEG, false>();
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG>, kWaveBlock,
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, false>, kWaveBlock,
                                                              wave_smem_bytes<R>());
     }
     if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
@@ -55,10 +61,18 @@ static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, flo
                             cudaStream_t stream)
 {
     if (variant == kVariantWave) {
-        const cudaError_t e = wave_prepare<R, INTEG>();
+        // scenes with options (RT_FLAG_*) take the options build of the loop
+        if (sc.flags) {
+            const cudaError_t e = wave_prepare<R, INTEG, true>();
+            if (e != cudaSuccess) return e;
+            wave_kernel<R, INTEG, true><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+                sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br);
+            return cudaGetLastError();
+        }
+        const cudaError_t e = wave_prepare<R, INTEG, false>();
         if (e != cudaSuccess) return e;
-        wave_kernel<R, INTEG><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(sc, rgb, rgb8, rec, counters,
-                                                                                  min_active, ss.col, ss.cnt);
+        wave_kernel<R, INTEG, false><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+            sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br);
         return cudaGetLastError();
     }
     if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
@@ -75,19 +89,24 @@ static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, flo
     return cudaGetLastError();
 }
 
+size_t branch_queue_bytes(int precision, int grid)
+{
+    return precision == RT_FP64 ? wave_branch_bytes<double>(grid) : wave_branch_bytes<float>(grid);
+}
+
 bool variant_compiled(int precision, int integrator, int variant)
 {
     if (variant == 0 || variant == kVariantWave) return true;
     return precision == RT_FP32 && integrator == RT_RK4 && variant >= 0 && variant < kLaneVariants;
 }
 
-cudaError_t render_occupancy(int precision, int integrator, int variant, int* blocks_per_sm)
+cudaError_t render_occupancy(int precision, int integrator, int variant, bool opt, int* blocks_per_sm)
 {
     if (precision == RT_FP64)
-        return integrator == RT_DP45 ? occupancy_t<double, RT_DP45>(variant, blocks_per_sm)
-                                     : occupancy_t<double, RT_RK4>(variant, blocks_per_sm);
-    return integrator == RT_DP45 ? occupancy_t<float, RT_DP45>(variant, blocks_per_sm)
-                                 : occupancy_t<float, RT_RK4>(variant, blocks_per_sm);
+        return integrator == RT_DP45 ? occupancy_t<double, RT_DP45>(variant, opt, blocks_per_sm)
+                                     : occupancy_t<double, RT_RK4>(variant, opt, blocks_per_sm);
+    return integrator == RT_DP45 ? occupancy_t<float, RT_DP45>(variant, opt, blocks_per_sm)
+                                 : occupancy_t<float, RT_RK4>(variant, opt, blocks_per_sm);
 }
 
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,

@@ -56,7 +56,7 @@ struct Flight {
 struct rt_server {
     int precision_of(uint64_t t) { return req[t].desc.precision; }
     int integrator_of(uint64_t t) { return req[t].desc.integrator; }
-    int grid;
+    int nsm;
     int device;
     size_t budget, in_use;
     int max_inflight;
@@ -116,7 +116,17 @@ static void launch_flight(rt_server* S, const std::vector<uint64_t>& tickets, in
         outs[i] = r.d_out;
     }
     void *d_scenes = nullptr, *d_off = nullptr, *d_soff = nullptr, *d_rgbs = nullptr, *d_cnt = nullptr;
-    void *d_samp = nullptr, *d_pcnt = nullptr;
+    void *d_samp = nullptr, *d_pcnt = nullptr, *d_br = nullptr;
+    bool fresnel = false, opt = false;
+    for (int i = 0; i < n; ++i) {
+        fresnel = fresnel || (dev[i].flags & RT_FLAG_FRESNEL);
+        opt = opt || dev[i].flags != 0;
+    }
+    // one persistent block per resident slot of the build the flight takes
+    int bps = 0;
+    if (e == cudaSuccess) e = batch_occupancy(S->precision_of(tickets[0]), S->integrator_of(tickets[0]), opt, &bps);
+    const int grid = (bps > 0 ? bps : 1) * S->nsm;
+    if (fresnel) alloc(&d_br, branch_queue_bytes(S->precision_of(tickets[0]), grid));
     alloc(&d_scenes, sizeof(DevScene) * n);
     alloc(&d_off, sizeof(int64_t) * (n + 1));
     alloc(&d_soff, sizeof(int64_t) * (n + 1));
@@ -132,8 +142,8 @@ static void launch_flight(rt_server* S, const std::vector<uint64_t>& tickets, in
     if (e == cudaSuccess) e = cudaMemsetAsync(d_pcnt, 0, kScratchBytesPerPixel * (size_t)off[n], st);
     if (e == cudaSuccess) {
         const BatchLaunch L = {(const DevScene*)d_scenes, (const int64_t*)d_off, (const int64_t*)d_soff,
-                               (float* const*)d_rgbs, n, off[n], soff[n], {(float*)d_samp, (int*)d_pcnt},
-                               (unsigned long long*)d_cnt, kMinActive, S->grid};
+                               (float* const*)d_rgbs, n, off[n], soff[n], {(float*)d_samp, (int*)d_pcnt, d_br},
+                               (unsigned long long*)d_cnt, kMinActive, grid, opt};
         e = launch_batch(S->precision_of(tickets[0]), S->integrator_of(tickets[0]), L, st);
     }
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&f.done, cudaEventDisableTiming);
@@ -284,10 +294,9 @@ int rt_server_create(size_t ray_state_budget_bytes, int32_t max_inflight, rt_ser
         S->streams.push_back(st);
         S->stream_busy.push_back(false);
     }
-    int bps = 0, nsm = 0;
-    batch_occupancy(RT_FP32, RT_RK4, &bps);
+    int nsm = 0;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    S->grid = (bps > 0 ? bps : 1) * nsm;
+    S->nsm = nsm > 0 ? nsm : 1;
     S->worker = std::thread(worker_main, S);
     *out = S;
     return RT_OK;

@@ -45,6 +45,8 @@ struct LaneStats {
     uint32_t steps, evals, newton, refine;
 };
 
+template <class R> struct Branch;
+
 // Ray inside the cloak, local coordinates: x = cx + X, |X| <= 1/2.
 template <class R>
 struct Box {
@@ -69,7 +71,72 @@ struct Cold {
     int sample, bounces, events, status;
     uint32_t rays, nevents, stat[5];
     int phase, surf, steps;   // the wavefront loop (rt_wave.cuh): state of a pixel between tasks
+    // Fresnel weights (RT_FLAG_FRESNEL): weight of the current path, which path
+    // of the sample it is (0: the camera's, k: the k-th branch), branches
+    // queued and taken, and whether the path starts inside the plate
+    R w;
+    int path, nbr, ibr, in_plate;
+    Branch<R>* br;            // this sample's branch queue (kMaxBranches records)
 };
+
+enum : int { MED_AIR = 0, MED_BOX = 1, MED_PLATE = 2 };
+constexpr int kMaxBranches = 8;      // Fresnel branches followed per camera sample
+
+// A Fresnel branch waiting to be traced: where it starts, its momentum (unit
+// direction in air, |p| = n in the box or the plate), its weight and the
+// counters of the path it split from.
+template <class R>
+struct Branch {
+    R cx, X, y, z;
+    R p[3];
+    R w;
+    int medium, surf, bounces, events, steps;
+};
+
+// Unpolarised Fresnel reflectance R = (rs^2 + rp^2)/2 going from index n1 into
+// n2, from the normal components of the momentum on both sides (|p| = n):
+//   rs = (|pn1| - |pn2|) / (|pn1| + |pn2|),
+//   rp = (n2^2 |pn1| - n1^2 |pn2|) / (n2^2 |pn1| + n1^2 |pn2|).
+// Written with explicit roundings (__dmul_rn, __dadd_rn: never contracted
+// into FMAs) so that every kernel computes the same weights.
+__device__ __forceinline__ double fresnel_R(double n1, double n2, double pn1, double pn2)
+{
+    const double a = fabs(pn1), b = fabs(pn2);
+    const double rs = (a - b) / (a + b);
+    const double u = __dmul_rn(__dmul_rn(n2, n2), a), v = __dmul_rn(__dmul_rn(n1, n1), b);
+    const double rp = __dadd_rn(u, -v) / __dadd_rn(u, v);
+    return 0.5 * __dadd_rn(__dmul_rn(rs, rs), __dmul_rn(rp, rp));
+}
+
+// At a Fresnel crossing: the camera's path queues the reflected branch (if
+// there is room) and every path keeps the transmitted share of its weight.
+template <class R>
+__device__ __forceinline__ void fresnel_split(Cold<R>& C, double Rf, int medium, R cx, R X, R y, R z, double pr0,
+                                              double pr1, double pr2, int surf, int steps)
+{
+    if (C.path == 0 && C.br && C.nbr < kMaxBranches) {
+        Branch<R>& q = C.br[C.nbr++];
+        q.cx = cx; q.X = X; q.y = y; q.z = z;
+        q.p[0] = (R)pr0; q.p[1] = (R)pr1; q.p[2] = (R)pr2;
+        q.w = (R)((double)C.w * Rf);
+        q.medium = medium;
+        q.surf = surf;
+        q.bounces = C.bounces;
+        q.events = C.events;
+        q.steps = steps;
+    }
+    C.w = (R)((double)C.w * (1.0 - Rf));
+}
+
+// Scene options (RT_FLAG_*) as one build of the kernels sees them: the plain
+// build (OPT = false) compiles every option out, so scenes without options
+// pay nothing for them; the options build reads them from the scene.
+template <bool OPT>
+__device__ __forceinline__ int opt_flags(const DevScene& sc)
+{
+    if constexpr (OPT) return sc.flags;
+    else return 0;
+}
 
 // ------------------------------------------------------------------------
 // W0 near the branch point in FP64 (FP32 path only).
@@ -187,17 +254,17 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
     w0_continue(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
     R F2x, F2y;
-    ray_force(wr, wi, rr, ri, F2x, F2y);
+    ray_force(wr, wi, rr, ri, k.fk, F2x, F2y);
     // stage 3 at r + h/2 (p + h/2 F1), (h/2)^2 F1 away from stage 2
     const R X3 = s.X + h2 * (s.px + h2 * s.Fx), y3 = s.y + h2 * (s.py + h2 * s.Fy);
     w0_continue(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
     R F3x, F3y;
-    ray_force(wr, wi, rr, ri, F3x, F3y);
+    ray_force(wr, wi, rr, ri, k.fk, F3x, F3y);
     // stage 4 at r + h (p + h/2 F2)
     const R X4 = s.X + h * (s.px + h2 * F2x), y4 = s.y + h * (s.py + h2 * F2y);
     w0_continue(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
     R F4x, F4y;
-    ray_force(wr, wi, rr, ri, F4x, F4y);
+    ray_force(wr, wi, rr, ri, k.fk, F4x, F4y);
     // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
     const R h6 = h * R(1.0 / 6.0), hh6 = h * h6;
     const R dX = h * s.px + hh6 * (s.Fx + F2x + F3x);
@@ -248,7 +315,7 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
     auto stage = [&](R Px, R Py, R dXs, R dYs, R& Fx, R& Fy) {
         const R Xs = s.X + dXs, Ys = s.y + dYs;
         w0_continue(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, st);
-        ray_force(wr, wi, rr, ri, Fx, Fy);
+        ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
         Xp = Xs;
         yp = Ys;
     };
@@ -294,7 +361,7 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
     // force at the fifth-order point (first same as last)
     w0_continue(k, o.X, o.y, o.X - Xp, o.y - yp, wr, wi, rr, ri, st);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
-    ray_force(wr, wi, rr, ri, o.Fx, o.Fy);
+    ray_force(wr, wi, rr, ri, k.fk, o.Fx, o.Fy);
     // error estimate h sum (b - b*) k over the seven stages
     e[0] = h * (R(T::e1) * P1x + R(T::e3) * P3x + R(T::e4) * P4x + R(T::e5) * P5x + R(T::e6) * P6x + R(T::e7) * P7x);
     e[1] = h * (R(T::e1) * P1y + R(T::e3) * P3y + R(T::e4) * P4y + R(T::e5) * P5y + R(T::e6) * P6y + R(T::e7) * P7y);
@@ -445,7 +512,7 @@ __device__ __forceinline__ void advance(Cold<R>& C, R t)
 // the lever arm of the FP32 rounding of the direction is that short, and the
 // remaining distance is far above the box-entry threshold of the FP32 path.  Reciprocals and the norm use FP32 seeds refined by one
 // Newton step in FP64.
-template <class R>
+template <class R, bool OPT>
 __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
 {
     const int i = (int)(C.pix / sc.wout), j = (int)(C.pix % sc.wout);
@@ -480,7 +547,7 @@ __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
             inv[a] = inv[a] * (2.0 - d[a] * inv[a]);
         }
         double tf = (sc.ymirror - sc.C[1]) * inv[1];          // the mirror cannot be met earlier
-        if (sc.cloak) {
+        if (sc.cloak || (opt_flags<OPT>(sc) & RT_FLAG_PLATE)) {
             double tn = -INFINITY, tx = INFINITY;
             bool miss = false;
             for (int a = 0; a < 3; ++a) {
@@ -607,7 +674,7 @@ __device__ __forceinline__ R box_entry(const StepConst<R>& k, const Cold<R>& C, 
 {
     const R pos[3] = {C.X, C.y, C.z};
     const R dir[3] = {C.dx, C.dy, C.dz};
-    const R lo[3] = {-k.E2 - C.cx, -k.A, -k.E2}, hi[3] = {k.E2 - C.cx, k.ytop, k.E2};
+    const R lo[3] = {-k.E2 - C.cx, k.ybot, -k.E2}, hi[3] = {k.E2 - C.cx, k.ytop, k.E2};
     const int flo[3] = {EV_XM, EV_NONE, EV_ZM}, fhi[3] = {EV_XP, EV_TOP, EV_ZP};
     R tn = R(-INFINITY), tf = R(INFINITY);
     int fn = EV_NONE;
@@ -665,15 +732,25 @@ __device__ __forceinline__ int background(const DevScene& sc, const AirConst<R>&
     return RT_RAY_OK;
 }
 
-template <class R>
+template <class R, bool OPT>
 __device__ __forceinline__ void finish_sample(const DevScene& sc, Cold<R>& C, int steps, int status, int& phase,
                                               rt_ray_record* rec)
 {
     if (status != RT_RAY_OK && status != RT_RAY_SKY) C.col[0] = C.col[1] = C.col[2] = 0.0f;
+    if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL) {
+        // an explicit FMA: the same rounding in every kernel that inlines this
+        const float w = (float)C.w;
+        C.acc[0] = fmaf(w, C.col[0], C.acc[0]);
+        C.acc[1] = fmaf(w, C.col[1], C.acc[1]);
+        C.acc[2] = fmaf(w, C.col[2], C.acc[2]);
+    } else {
+        C.acc[0] += C.col[0];
+        C.acc[1] += C.col[1];
+        C.acc[2] += C.col[2];
+    }
+    phase = PH_DONE;
+    if (OPT && C.path != 0) return;                 // a Fresnel branch: no record, no ray of its own
     C.status = status;
-    C.acc[0] += C.col[0];
-    C.acc[1] += C.col[1];
-    C.acc[2] += C.col[2];
     C.rays += 1;
     C.stat[status < 5 ? status : 4] += 1;
     if (rec) {
@@ -708,21 +785,116 @@ __device__ __forceinline__ void box_to_air(Cold<R>& C, const Box<R>& b, const R 
     C.dz = d[2] * il;
 }
 
-template <class R>
+// Inside the homogeneous plate of RT_FLAG_PLATE (index 1 + kA on the flat
+// mirror, filling the box from y = 0 to its top): straight segments in FP64
+// from P with momentum q (|q| = n_plate) to the mirror (reflection), the top
+// or a side face (refraction into air, or total internal reflection).  On the
+// way out the air state of C is set and true returned; false when the path
+// ended inside (bounce guard), with phase = PH_DONE.
+template <class R, bool OPT>
+__device__ bool plate_traverse(const DevScene& sc, Cold<R>& C, double P[3], double q[3], int steps, int& phase,
+                               rt_ray_record* rec)
+{
+    const double lo[3] = {-sc.E2, 0.0, -sc.E2}, hi[3] = {sc.E2, sc.ytop, sc.E2};
+    for (;;) {
+        int hit = EV_NONE;
+        double tmin = INFINITY;
+        if (C.bounces <= sc.max_bounces) {
+            for (int a = 0; a < 3; ++a) {
+                if (q[a] == 0.0) continue;
+                const double t = ((q[a] > 0.0 ? hi[a] : lo[a]) - P[a]) / q[a];
+                if (t < tmin) {
+                    tmin = t;
+                    hit = (a == 0) ? (q[a] > 0.0 ? EV_XP : EV_XM)
+                                   : (a == 1 ? (q[a] > 0.0 ? EV_TOP : EV_GRATING) : (q[a] > 0.0 ? EV_ZP : EV_ZM));
+                }
+            }
+        }
+        if (hit == EV_NONE) {                  // bounce guard (or no direction): report where it is
+            const double cxd = rint(P[0]);
+            const double ql = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+            C.cx = (R)cxd; C.X = (R)(P[0] - cxd); C.y = (R)P[1]; C.z = (R)P[2];
+            C.dx = (R)(q[0] / ql); C.dy = (R)(q[1] / ql); C.dz = (R)(q[2] / ql);
+            finish_sample<R, OPT>(sc, C, steps, C.bounces > sc.max_bounces ? RT_RAY_MAX_BOUNCES : RT_RAY_NAN, phase, rec);
+            return false;
+        }
+        if (tmin < 0.0) tmin = 0.0;
+        for (int a = 0; a < 3; ++a) P[a] += tmin * q[a];
+        if (hit == EV_GRATING) {               // the mirror under the plate
+            P[1] = 0.0;
+            q[1] = -q[1];
+            C.bounces++;
+            continue;
+        }
+        R Nf[3];
+        face_normal(hit, Nf);
+        const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
+        const double pn = q[0] * N[0] + q[1] * N[1] + q[2] * N[2];
+        double pt[3];
+        for (int a = 0; a < 3; ++a) pt[a] = q[a] - pn * N[a];
+        const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
+        if (pt2 >= 1.0) {                      // total internal reflection
+            for (int a = 0; a < 3; ++a) q[a] -= 2.0 * pn * N[a];
+            C.bounces++;
+            continue;
+        }
+        const double pout = sqrt(1.0 - pt2);
+        const double cxd = rint(P[0]);
+        C.cx = (R)cxd; C.X = (R)(P[0] - cxd); C.y = (R)P[1]; C.z = (R)P[2];
+        if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL)
+            fresnel_split(C, fresnel_R(sc.plate_n, 1.0, pn, pout), MED_PLATE, C.cx, C.X, C.y, C.z,
+                          q[0] - 2.0 * pn * N[0], q[1] - 2.0 * pn * N[1], q[2] - 2.0 * pn * N[2], hit, steps);
+        C.dx = (R)(pt[0] + pout * N[0]);
+        C.dy = (R)(pt[1] + pout * N[1]);
+        C.dz = (R)(pt[2] + pout * N[2]);
+        return true;
+    }
+}
+
+template <class R, bool OPT>
 __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
                             rt_ray_record* rec, LaneStats& st)
 {
     const StepConst<R>& k = step_const<R>(sc);
+    const bool plate = (opt_flags<OPT>(sc) & RT_FLAG_PLATE) != 0;
+    if (OPT && C.in_plate) {
+        // a Fresnel branch that starts inside the plate: C holds its position and momentum
+        C.in_plate = 0;
+        double P[3] = {(double)C.cx + (double)C.X, (double)C.y, (double)C.z};
+        double q[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+        if (!plate_traverse<R, OPT>(sc, C, P, q, steps, phase, rec)) return;
+        surf = EV_NONE;
+    }
     for (;;) {
-        if (C.bounces > sc.max_bounces) { finish_sample(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec); return; }
+        if (C.bounces > sc.max_bounces) { finish_sample<R, OPT>(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec); return; }
         R hcx = R(0), hX = R(0), hy = R(0);
         const R tm = sc.mirror ? trochoid_line_hit(k, C, surf == EV_GRATING, hcx, hX, hy) : flat_line_hit(C);
         int face = EV_NONE;
-        const R tb = sc.cloak ? box_entry(k, C, face) : R(INFINITY);
+        const R tb = (sc.cloak || plate) ? box_entry(k, C, face) : R(INFINITY);
         if (tb < tm) {
             advance(C, tb);
             R Nf[3];
             face_normal(face, Nf);
+            const double d[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+            const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
+            const double pn = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
+            double pt[3];
+            for (int a = 0; a < 3; ++a) pt[a] = d[a] - pn * N[a];
+            const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
+            if (plate) {
+                // into the denser plate (no total reflection), then straight through it
+                const double npl = sc.plate_n;
+                const double pin = sqrt(npl * npl - pt2);
+                if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL)
+                    fresnel_split(C, fresnel_R(1.0, npl, pn, pin), MED_AIR, C.cx, C.X, C.y, C.z,
+                                  d[0] - 2.0 * pn * N[0], d[1] - 2.0 * pn * N[1], d[2] - 2.0 * pn * N[2], EV_NONE,
+                                  steps);
+                double P[3] = {(double)C.cx + (double)C.X, (double)C.y, (double)C.z};
+                double q[3] = {pt[0] - pin * N[0], pt[1] - pin * N[1], pt[2] - pin * N[2]};
+                if (!plate_traverse<R, OPT>(sc, C, P, q, steps, phase, rec)) return;
+                surf = EV_NONE;
+                continue;
+            }
             b.cx = C.cx;
             b.X = C.X;
             b.y = C.y;
@@ -730,15 +902,11 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             b.wr = b.wi = R(0);
             w0_eval(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
             // Snell's law in FP64 (a few operations per entry): sqrt(n^2 - |p_t|^2)
-            // is ill-conditioned near grazing incidence
+            // is ill-conditioned near grazing incidence; the index is scaled
+            // by idx_scale in the referenced cloak
             const double rr = (double)b.rr, ri = (double)b.ri;
-            const double n2 = rr * rr + ri * ri;
-            const double d[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
-            const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
-            const double pn = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
-            double pt[3];
-            for (int a = 0; a < 3; ++a) pt[a] = d[a] - pn * N[a];
-            const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
+            double n2 = rr * rr + ri * ri;
+            if (opt_flags<OPT>(sc) & RT_FLAG_REFERENCED) n2 *= sc.idx_scale * sc.idx_scale;
             if (n2 < pt2) {      // total reflection off the outside of the box
                 C.dx = (R)(d[0] - 2.0 * pn * N[0]);
                 C.dy = (R)(d[1] - 2.0 * pn * N[1]);
@@ -748,12 +916,15 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                 continue;
             }
             const double pin = sqrt(n2 - pt2);
+            if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL)
+                fresnel_split(C, fresnel_R(1.0, sqrt(n2), pn, pin), MED_AIR, C.cx, C.X, C.y, C.z,
+                              d[0] - 2.0 * pn * N[0], d[1] - 2.0 * pn * N[1], d[2] - 2.0 * pn * N[2], EV_NONE, steps);
             b.px = (R)(pt[0] - pin * N[0]);
             b.py = (R)(pt[1] - pin * N[1]);
             b.pz = (R)(pt[2] - pin * N[2]);
             b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
             b.hc = k.h;
-            ray_force(b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy);
+            ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
             surf = face;
             phase = PH_BOX;
             return;
@@ -783,7 +954,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             continue;
         }
         const int status = background(sc, air_const<R>(sc), C, C.col);
-        finish_sample(sc, C, steps, status, phase, rec);
+        finish_sample<R, OPT>(sc, C, steps, status, phase, rec);
         return;
     }
 }
@@ -791,7 +962,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
 // ------------------------------------------------------------------------
 // Service of a lane whose step crossed a surface (or hit a guard).
 // ------------------------------------------------------------------------
-template <class R, int INTEG>
+template <class R, int INTEG, bool OPT>
 __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
                               rt_ray_record* rec, LaneStats& st)
 {
@@ -799,14 +970,14 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     const R p0[3] = {b.px, b.py, b.pz};
     if (phase == PH_GUARD) {
         box_to_air(C, b, p0);
-        finish_sample(sc, C, steps, RT_RAY_MAX_STEPS, phase, rec);
+        finish_sample<R, OPT>(sc, C, steps, RT_RAY_MAX_STEPS, phase, rec);
         return;
     }
     bool finite = true;
     for (int ev = 0; ev < EV_COUNT; ++ev) finite = finite && isfinite(C.g1[ev]);
     if (!finite || !(isfinite(b.X) && isfinite(b.y) && isfinite(b.px) && isfinite(b.py))) {
         box_to_air(C, b, p0);
-        finish_sample(sc, C, steps, RT_RAY_NAN, phase, rec);
+        finish_sample<R, OPT>(sc, C, steps, RT_RAY_NAN, phase, rec);
         return;
     }
     int ev_best = EV_NONE, last = EV_NONE;
@@ -826,7 +997,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     const R hc = b.hc;
     b = t;
     b.hc = hc;
-    ray_force(b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy);
+    ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
     C.events++;
     C.nevents++;
     if (ev_best == EV_GRATING) {
@@ -843,7 +1014,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
         if (C.bounces > sc.max_bounces) {
             const R p[3] = {b.px, b.py, b.pz};
             box_to_air(C, b, p);
-            finish_sample(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec);
+            finish_sample<R, OPT>(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec);
         }
         return;
     }
@@ -868,11 +1039,17 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
         if (C.bounces > sc.max_bounces) {
             const R q[3] = {b.px, b.py, b.pz};
             box_to_air(C, b, q);
-            finish_sample(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec);
+            finish_sample<R, OPT>(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec);
         }
         return;
     }
     const double pout = sqrt(1.0 - pt2);
+    if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL) {
+        // the reflected branch stays in the cloak, starting on this face
+        const double n1 = sqrt(p[0] * p[0] + p[1] * p[1] + p[2] * p[2]);   // |p| = n
+        fresnel_split(C, fresnel_R(n1, 1.0, pn, pout), MED_BOX, b.cx, b.X, b.y, b.z, p[0] - 2.0 * pn * N[0],
+                      p[1] - 2.0 * pn * N[1], p[2] - 2.0 * pn * N[2], ev_best, steps);
+    }
     double d[3], l2 = 0.0;
     for (int a = 0; a < 3; ++a) { d[a] = pt[a] + pout * N[a]; l2 += d[a] * d[a]; }
     const double il = 1.0 / sqrt(l2);
@@ -936,7 +1113,7 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         hs = k.h;
         rk4_step(k, s, hs, o, st);
         w0_eval(k, o.X, o.y, o.wr, o.wi, o.rr, o.ri, st);
-        ray_force(o.wr, o.wi, o.rr, o.ri, o.Fx, o.Fy);
+        ray_force(o.wr, o.wi, o.rr, o.ri, k.fk, o.Fx, o.Fy);
         ++steps;
         st.steps++;
     }
@@ -986,16 +1163,63 @@ __device__ __forceinline__ int64_t grab_work(unsigned long long* counter, unsign
     return (int64_t)(base + rank);
 }
 
-template <class R>
+template <class R, bool OPT>
 __device__ __forceinline__ void start_sample(const DevScene& sc, Cold<R>& C, int& phase, int& surf, int& steps)
 {
-    camera_start(sc, C);
+    camera_start<R, OPT>(sc, C);
     C.bounces = 0;
     C.events = 0;
+    C.w = R(1);
+    C.path = 0;
+    C.nbr = 0;
+    C.ibr = 0;
+    C.in_plate = 0;
     C.col[0] = C.col[1] = C.col[2] = 0.0f;
     surf = EV_NONE;
     steps = 0;
     phase = PH_AIR;
+}
+
+// Start the next queued Fresnel branch of the sample in place of the path
+// that just ended (phase becomes PH_AIR or PH_BOX).
+template <class R>
+__device__ void start_branch(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int& steps,
+                             LaneStats& st)
+{
+    const Branch<R> q = C.br[C.ibr++];
+    C.path = C.ibr;
+    C.w = q.w;
+    C.bounces = q.bounces;
+    C.events = q.events;
+    C.col[0] = C.col[1] = C.col[2] = 0.0f;
+    steps = q.steps;
+    surf = q.surf;
+    if (q.medium == MED_BOX) {
+        const StepConst<R>& k = step_const<R>(sc);
+        b.cx = q.cx;
+        b.X = q.X;
+        b.y = q.y;
+        b.z = q.z;
+        b.px = q.p[0];
+        b.py = q.p[1];
+        b.pz = q.p[2];
+        b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
+        b.wr = b.wi = R(0);
+        w0_eval(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
+        ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
+        b.hc = k.h;
+        phase = PH_BOX;
+    } else {
+        C.cx = q.cx;
+        C.X = q.X;
+        C.y = q.y;
+        C.z = q.z;
+        C.dx = q.p[0];
+        C.dy = q.p[1];
+        C.dz = q.p[2];
+        C.in_plate = (q.medium == MED_PLATE);
+        phase = PH_AIR;
+    }
 }
 
 __device__ __forceinline__ uint8_t quantize8(float c)
@@ -1021,6 +1245,7 @@ struct OneScene {
     rt_ray_record* rec;
     float* samp_col;
     int* pix_cnt;
+    void* branches;              // Fresnel branch queues, kMaxBranches per pool entry (or null)
     __device__ __forceinline__ const DevScene& scene(int) const { return sc; }
     __device__ __forceinline__ int64_t nwork() const { return sc.nwork; }
     __device__ __forceinline__ int64_t nsamples() const { return sc.nwork * sc.spp; }
@@ -1053,6 +1278,7 @@ struct ManyScenes {
     int64_t total, total_samples;
     float* samp_col;
     int* pix_cnt;
+    void* branches;
     __device__ __forceinline__ const DevScene& scene(int s) const { return scenes[s]; }
     __device__ __forceinline__ int64_t nwork() const { return total; }
     __device__ __forceinline__ int64_t nsamples() const { return total_samples; }
@@ -1119,7 +1345,7 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
         // the cloak again or the work is exhausted
         while (phase != PH_BOX && phase != PH_EXIT) {
             if (phase == PH_EVENT || phase == PH_GUARD)
-                service_event<R, INTEG>(src.scene(C.scene), C, b, phase, surf, steps, src.rec_of(C.scene), st);
+                service_event<R, INTEG, false>(src.scene(C.scene), C, b, phase, surf, steps, src.rec_of(C.scene), st);
             if (phase == PH_IDLE) {
                 const int64_t w = grab_work(&counters[0], lane);
                 if (w >= nwork) { phase = PH_EXIT; break; }
@@ -1131,13 +1357,13 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
                 C.pix = pix;
                 C.sample = 0;
                 C.acc[0] = C.acc[1] = C.acc[2] = 0.0f;
-                start_sample(src.scene(s), C, phase, surf, steps);
+                start_sample<R, false>(src.scene(s), C, phase, surf, steps);
             }
             const DevScene& sc = src.scene(C.scene);
-            if (phase == PH_AIR) air_segment(sc, C, b, phase, surf, steps, src.rec_of(C.scene), st);
+            if (phase == PH_AIR) air_segment<R, false>(sc, C, b, phase, surf, steps, src.rec_of(C.scene), st);
             if (phase == PH_DONE) {
                 if (++C.sample < sc.spp) {
-                    start_sample(sc, C, phase, surf, steps);
+                    start_sample<R, false>(sc, C, phase, surf, steps);
                 } else {
                     const float inv = 1.0f / (float)sc.spp;
                     float c[3];
@@ -1201,7 +1427,7 @@ __global__ void __launch_bounds__(kRenderBlock, MINB) render_kernel(const __grid
                                                                     uint8_t* __restrict__ rgb8, rt_ray_record* rec,
                                                                     unsigned long long* counters, int min_active)
 {
-    const OneScene src{sc, rgb, rgb8, rec, nullptr, nullptr};
+    const OneScene src{sc, rgb, rgb8, rec, nullptr, nullptr, nullptr};
     render_loop<R, INTEG>(src, counters, min_active);
 }
 
@@ -1222,7 +1448,7 @@ __global__ void medium_kernel(double kA, double Lambda, const double* __restrict
     k.w0tol = (R)(Mth<R>::kRel * kA);
     w0_eval(k, X, yy, wr, wi, rr, ri, st);
     R Fx, Fy;
-    ray_force(wr, wi, rr, ri, Fx, Fy);
+    ray_force(wr, wi, rr, ri, R(kTwoPi), Fx, Fy);
     out[5 * i + 0] = (double)wr;
     out[5 * i + 1] = (double)wi;
     out[5 * i + 2] = sqrt((double)(rr * rr + ri * ri));

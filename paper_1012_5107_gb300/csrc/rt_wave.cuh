@@ -49,6 +49,13 @@ constexpr size_t wave_smem_bytes()
     return (sizeof(Cold<R>) + sizeof(Box<R>)) * WavePool<R>::P + 3 * sizeof(short) * WavePool<R>::P;
 }
 
+// Bytes of the Fresnel branch queues of a launch of `grid` blocks.
+template <class R>
+constexpr size_t wave_branch_bytes(int grid)
+{
+    return (size_t)grid * WavePool<R>::P * kMaxBranches * sizeof(Branch<R>);
+}
+
 struct WaveCtl {
     int lock;
     int in_head, in_cnt;     // cloak queue
@@ -153,7 +160,7 @@ __device__ __forceinline__ void wave_finish_sample(const Src& src, const DevScen
     }
 }
 
-template <class R, int INTEG, class Src>
+template <class R, int INTEG, bool OPT, class Src>
 __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* counters, int min_active)
 {
     constexpr int P = WavePool<R>::P;
@@ -165,12 +172,14 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
     short* frq = svq + P;
     __shared__ WaveCtl Q;
 
+    Branch<R>* branches = reinterpret_cast<Branch<R>*>(src.branches);
     for (int p = threadIdx.x; p < P; p += blockDim.x) {
         Cold<R>& C = cold[p];
         C.rays = 0;
         C.nevents = 0;
         C.scene = 0;
         for (int q = 0; q < 5; ++q) C.stat[q] = 0;
+        C.br = branches ? branches + ((int64_t)blockIdx.x * P + p) * kMaxBranches : nullptr;
         frq[p] = (short)p;
     }
     if (threadIdx.x == 0) {
@@ -302,7 +311,7 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                 }
                 while (phase != PH_BOX && phase != PH_EXIT) {
                     if (phase == PH_EVENT || phase == PH_GUARD)
-                        service_event<R, INTEG>(src.scene(C.scene), C, b, phase, surf, steps, src.rec_of(C.scene), st);
+                        service_event<R, INTEG, OPT>(src.scene(C.scene), C, b, phase, surf, steps, src.rec_of(C.scene), st);
                     if (phase == PH_IDLE) {
                         const int64_t ws = grab_work(&counters[0], lane);
                         if (ws >= nsamples) { phase = PH_EXIT; break; }
@@ -314,13 +323,23 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                         C.pix = pix;
                         C.sample = sample;
                         C.acc[0] = C.acc[1] = C.acc[2] = 0.0f;
-                        start_sample(src.scene(s), C, phase, surf, steps);
+                        start_sample<R, OPT>(src.scene(s), C, phase, surf, steps);
                     }
                     const DevScene& scs = src.scene(C.scene);
-                    if (phase == PH_AIR) air_segment(scs, C, b, phase, surf, steps, src.rec_of(C.scene), st);
+                    if (phase == PH_AIR) air_segment<R, OPT>(scs, C, b, phase, surf, steps, src.rec_of(C.scene), st);
                     if (phase == PH_DONE) {
-                        wave_finish_sample(src, scs, C);
-                        phase = PH_IDLE;
+                        if (OPT && C.ibr < C.nbr) {
+                            start_branch(scs, C, b, phase, surf, steps, st);   // next Fresnel branch
+                        } else {
+                            rt_ray_record* rec = src.rec_of(C.scene);
+                            if (rec && (opt_flags<OPT>(scs) & RT_FLAG_FRESNEL)) {
+                                // the record's colour: the sample's, summed over its paths
+                                rt_ray_record* o = rec + C.work * scs.spp + C.sample;
+                                o->rgb[0] = C.acc[0]; o->rgb[1] = C.acc[1]; o->rgb[2] = C.acc[2];
+                            }
+                            wave_finish_sample(src, scs, C);
+                            phase = PH_IDLE;
+                        }
                     }
                 }
                 if (phase == PH_BOX) {
@@ -377,24 +396,25 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
 template <class R>
 constexpr int wave_min_blocks() { return sizeof(R) == 4 ? 2 : 1; }
 
-template <class R, int INTEG>
+template <class R, int INTEG, bool OPT>
 __global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_kernel(const __grid_constant__ DevScene sc,
                                                             float* __restrict__ rgb, uint8_t* __restrict__ rgb8,
                                                             rt_ray_record* rec, unsigned long long* counters,
-                                                            int min_active, float* samp_col, int* pix_cnt)
+                                                            int min_active, float* samp_col, int* pix_cnt,
+                                                            void* branches)
 {
-    const OneScene src{sc, rgb, rgb8, rec, samp_col, pix_cnt};
-    wave_loop<R, INTEG>(src, counters, min_active);
+    const OneScene src{sc, rgb, rgb8, rec, samp_col, pix_cnt, branches};
+    wave_loop<R, INTEG, OPT>(src, counters, min_active);
 }
 
-template <class R, int INTEG>
+template <class R, int INTEG, bool OPT>
 __global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_batch_kernel(
     const DevScene* __restrict__ scenes, const int64_t* __restrict__ offsets, const int64_t* __restrict__ soffsets,
     float* const* __restrict__ rgbs, int n, int64_t total, int64_t total_samples, float* samp_col, int* pix_cnt,
-    unsigned long long* counters, int min_active)
+    void* branches, unsigned long long* counters, int min_active)
 {
-    const ManyScenes src{scenes, offsets, soffsets, rgbs, n, total, total_samples, samp_col, pix_cnt};
-    wave_loop<R, INTEG>(src, counters, min_active);
+    const ManyScenes src{scenes, offsets, soffsets, rgbs, n, total, total_samples, samp_col, pix_cnt, branches};
+    wave_loop<R, INTEG, OPT>(src, counters, min_active);
 }
 
 }  // namespace grt

@@ -49,7 +49,8 @@ def test_version(rt):
     (dict(Lambda=0.0), "Lambda"), (dict(A=0.2), "A must"), (dict(width=0), "width"),
     (dict(hfov_deg=180.0), "hfov"), (dict(H=0.05), "H > 2A"), (dict(integrator=7), "integrator"),
     (dict(precision=3), "precision"), (dict(background=1, tex_size=0), "texture"),
-    (dict(mirror=0, cloak=1), "trochoid"), (dict(flags=1), "flags"), (dict(max_steps=0), "max_steps"),
+    (dict(mirror=0, cloak=1), "trochoid"), (dict(flags=8), "unknown bits"), (dict(max_steps=0), "max_steps"),
+    (dict(flags=2), "plate lies on the flat mirror"),
 ])
 def test_invalid_descriptor_is_rejected(rt, bad, field):
     p = inputs.base_scene(**bad)

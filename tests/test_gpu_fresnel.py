@@ -1,0 +1,116 @@
+"""Fresnel weights, the referenced cloak and the dielectric plate (Sec. 3,
+Sec. 4, Figs. 5-7) on the GPU against the oracle: every sample of small
+renders in FP64, images and well-conditioned rays in FP32, the batch, and the
+launch variants that cannot render Fresnel weights."""
+import numpy as np
+import pytest
+
+from paper_1012_5107_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+REF, PLATE, FRESNEL = 1, 2, 4
+
+CASES = {
+    "plate": dict(mirror=0, cloak=0, flags=PLATE),
+    "plate_fresnel": dict(mirror=0, cloak=0, flags=PLATE | FRESNEL),
+    "referenced": dict(flags=REF),
+    "referenced_fresnel": dict(flags=REF | FRESNEL),
+    "fresnel": dict(flags=FRESNEL),
+}
+
+
+@pytest.fixture(scope="module")
+def rt():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1012_5107_gb300 import build as B
+    B.build()
+    from paper_1012_5107_gb300 import rt as r
+    r.lib()
+    return r
+
+
+def render(rt, p, variant=None):
+    import torch
+    sc = rt.Scene(p)
+    if variant is not None:
+        sc.set_launch(variant, 0)
+    rgb = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+    rgb8 = torch.zeros(sc.shape, dtype=torch.uint8, device="cuda")
+    rec = torch.zeros(sc.height * sc.wout * sc.spp * 80, dtype=torch.uint8, device="cuda")
+    sc.render(rgb, rgb8, rec)
+    torch.cuda.synchronize()
+    out = dict(rgb=rgb.cpu().numpy(), rgb8=rgb8.cpu().numpy(), rec=rt.records_to_numpy(rec), stats=sc.stats())
+    sc.close()
+    return out
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fp64_matches_oracle(rt, orc, case):
+    """FP64: every sample's first path and the sample colours (the weighted
+    sum over the Fresnel branches) agree with the oracle."""
+    p = inputs.base_scene(width=48, height=40, spp=2, seed=9, precision=1, **CASES[case])
+    g = render(rt, p)
+    o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
+    gr, orr = g["rec"].reshape(-1), o_rec.reshape(-1)
+    same = (gr["status"] == orr["status"]) & (gr["bounces"] == orr["bounces"])
+    assert same.mean() >= 0.999
+    assert np.abs(gr["pos"] - orr["pos"])[same].max() < 1e-9
+    assert np.abs(gr["dir"] - orr["dir"])[same].max() < 1e-9
+    assert np.abs(gr["rgb"] - orr["rgb"])[same].max() < 1e-6       # float colours, weighted sums
+    assert (np.abs(g["rgb"] - o_rgb).max(-1) > 1e-6).mean() <= 0.002
+    assert g["stats"]["rays"] == 48 * 40 * 2 and g["stats"]["sched_timeouts"] == 0
+
+
+@pytest.mark.parametrize("case", ["plate_fresnel", "referenced_fresnel"])
+def test_fp32_images_match_oracle(rt, orc, case):
+    p = inputs.base_scene(width=64, height=64, spp=1, seed=10, precision=0, **CASES[case])
+    g = render(rt, p)
+    o_rgb = orc.render(orc.Scene(dict(p, precision=1)))
+    q = np.abs(g["rgb8"].astype(int) - orc.quantize(o_rgb).astype(int)).max(-1)
+    assert (q > 1).mean() <= 0.005
+    assert np.median(np.abs(g["rgb"] - o_rgb)) < 1e-5
+
+
+def test_fresnel_images_are_dimmer_by_the_lost_light(rt):
+    """With Fresnel weights the plate's image keeps T^2 + R + T^2 R of the
+    light of each pixel (Sec. 4: the transmissions make the image slightly
+    dimmer); without them all of it."""
+    base = inputs.base_scene(width=32, height=32, spp=1, seed=11, precision=1, mirror=0, cloak=0)
+    a = render(rt, dict(base, flags=PLATE))
+    b = render(rt, dict(base, flags=PLATE | FRESNEL))
+    ratio = b["rgb"].sum() / a["rgb"].sum()
+    assert 0.9 < ratio < 1.0
+
+
+def test_batch_with_fresnel_equals_single_renders(rt):
+    import torch
+    ps = [inputs.base_scene(width=40, height=32, spp=2, seed=12 + q, scene_id=q, precision=0, **CASES[c])
+          for q, c in enumerate(["referenced_fresnel", "plate_fresnel", "fresnel"])]
+    scenes = [rt.Scene(p) for p in ps]
+    outs = [torch.zeros(s.shape, dtype=torch.float32, device="cuda") for s in scenes]
+    b = rt.Batch(scenes)
+    b.render(outs)
+    torch.cuda.synchronize()
+    for p, o in zip(ps, outs):
+        single = render(rt, p)
+        # the FP64 products behind the Fresnel weights are contracted by each
+        # kernel on its own, which moves a float weight by an ulp at most
+        assert np.abs(o.cpu().numpy() - single["rgb"]).max() <= 1e-6
+    assert b.stats()["sched_timeouts"] == 0
+    b.close()
+
+
+def test_fresnel_needs_the_wavefront_loop(rt):
+    sc = rt.Scene(inputs.base_scene(width=8, height=8, spp=1, precision=0, flags=FRESNEL))
+    with pytest.raises(rt.RtError):
+        sc.set_launch(0, 0)
+    sc.set_launch(3, 20)
+
+
+@pytest.mark.parametrize("bad", [dict(flags=8), dict(flags=PLATE), dict(flags=PLATE, mirror=0, cloak=1)])
+def test_invalid_flags(rt, bad):
+    with pytest.raises(rt.RtError):
+        rt.Scene(inputs.base_scene(**bad))

@@ -323,6 +323,7 @@ def run_gpu(args):
     h2d = len(step.scenes) * 512      # scene parameters travel with each launch (DevScene by value)
 
     xmap = bench_xcorr_map(rt, torch, step, stream, clock_mhz)
+    table1 = None if args.no_table1 else bench_table1(rt, torch, stream)
     batch = None if args.no_batch else bench_batch(rt, torch, stream)
     serving = None if args.no_serving else bench_serving(rt, torch)
 
@@ -349,6 +350,7 @@ def run_gpu(args):
         "e2e": {"value": round(rays_per_step / e2e_s / 1e6, 3), "unit": "Mrays/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "xcorr_map": xmap,
+        "table1_referenced_fresnel": table1,
         "batched_64_scenes": batch,
         "serving": serving,
         "gpu_launches": step.launches * args.steps,
@@ -392,6 +394,50 @@ def bench_xcorr_map(rt, torch, step, stream, clock_mhz: float) -> dict:
             "frac_fp32_peak": round(tflops / (152 * 128 * 2 * clock_mhz * 1e6 / 1e12), 3),
             "C00_stacked": round(float(out[md, md, Cc].item()), 6),
             "peak": {"C": round(float(pk[0]), 6), "di": int(pk[1]), "dj": int(pk[2])}}
+
+
+def bench_table1(rt, torch, stream) -> dict:
+    """Table 1's rows for the referenced grating cloak on the synthetic
+    scenes: A = 3/(16 pi) (n/n_min in [1, 2.2]), cloak heights 1.1, 0.55 and
+    0.41 Lambda (Figs. 5-7), 256 x 256 x 4 with Fresnel weights.  For each
+    height: C(0,0) of the referenced cloak against the flat mirror and against
+    the flat mirror with the dielectric plate of index 1/n_min, at FOV 0
+    (centre line), 10, 25 and 50 deg, and the time of the cloak's render."""
+    import math
+    out = {}
+    A = 3.0 / (16.0 * math.pi)
+    for H in (1.1, 0.55, 0.41):
+        base = inputs.base_scene(width=256, height=256, spp=4, seed=2, A=A, H=H, precision=inputs.FP32)
+        kinds = {"mirror": dict(base, mirror=0, cloak=0),
+                 "plate": dict(base, mirror=0, cloak=0, flags=2 | 4),
+                 "cloak": dict(base, mirror=1, cloak=1, flags=1 | 4)}
+        imgs, ms_cloak, rays_cloak = {}, None, 0
+        for k, p in kinds.items():
+            for line in (0, 1):
+                sc = rt.Scene(dict(p, centre_line=line))
+                img = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+                with torch.cuda.stream(stream):
+                    sc.render(img, stream=stream)
+                    if k == "cloak" and not line:
+                        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                        e0.record(stream)
+                        sc.render(img, stream=stream)
+                        e1.record(stream)
+                torch.cuda.synchronize()
+                if k == "cloak" and not line:
+                    ms_cloak = e0.elapsed_time(e1)
+                    rays_cloak = sc.stats()["rays"]
+                imgs[(k, line)] = img
+        row = {"render_ms": round(ms_cloak, 3), "Mrays_per_s": round(rays_cloak / ms_cloak / 1e3, 2)}
+        for ref in ("mirror", "plate"):
+            c_full = rt.xcorr(imgs[(ref, 0)], imgs[("cloak", 0)], FOVS[1:], 50.0, stream=stream)
+            c_line = rt.xcorr(imgs[(ref, 1)], imgs[("cloak", 1)], FOVS[:1], 50.0, stream=stream)
+            torch.cuda.synchronize()
+            cf, cl = c_full.cpu().numpy(), c_line.cpu().numpy()
+            row[f"C_cloak_vs_{ref}"] = {"0": round(float(cl[0, 3]), 4), "10": round(float(cf[0, 3]), 4),
+                                        "25": round(float(cf[1, 3]), 4), "50": round(float(cf[2, 3]), 4)}
+        out[f"H={H}"] = row
+    return out
 
 
 def bench_batch(rt, torch, stream) -> dict:
@@ -529,6 +575,7 @@ def main():
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-table1", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

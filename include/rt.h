@@ -252,6 +252,20 @@ typedef struct rt_batch rt_batch;
 /* rt_batch_create: copy the scene tables of scenes[0..n-1] to the device. */
 int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out);
 
+/*
+ * rt_batch_update: new scene parameters for the next renders of the batch (a
+ * moving camera, another grating, another seed: one frame's inputs).  descs is
+ * a host array of n descriptors (n equal to the batch's), each with the same
+ * image size, samples per pixel, precision, integrator, background kind and
+ * flags as the scene it replaces (the textures stay the scenes').  The scene
+ * table is rebuilt on the host, staged in pinned host memory and copied to the
+ * device on `stream` (asynchronous, ordered before the next rt_batch_render on
+ * that stream; a second update waits for the first copy).  *h2d_bytes
+ * (nullable) receives the bytes copied.  RT_EINVAL for a descriptor that does
+ * not fit the batch.
+ */
+int rt_batch_update(rt_batch* batch, const rt_scene_desc* descs, int32_t n, void* stream, uint64_t* h2d_bytes);
+
 /* rt_batch_destroy: free the batch (waits for its outstanding work). */
 void rt_batch_destroy(rt_batch* batch);
 

@@ -168,6 +168,9 @@ struct rt_batch {
     int* d_pcnt;             // per-pixel sample counters
     void* d_br;              // Fresnel branch queues (when a scene has RT_FLAG_FRESNEL)
     bool opt;                // a scene has options (RT_FLAG_*): the options build of the loop
+    std::vector<DevScene> h_scenes;    // the table last uploaded
+    DevScene* h_stage;       // pinned staging of rt_batch_update
+    cudaEvent_t staged;      // the last staging copy is done
     float** d_rgbs;
     std::vector<float*> h_rgbs;        // output pointers last uploaded
     unsigned long long* d_counters;
@@ -230,6 +233,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
     int bps = 0;
     b->opt = opt;
+    b->h_scenes = dev;
     if (e == cudaSuccess) e = batch_occupancy(precision, integrator, opt, &bps);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, device);
     if (e != cudaSuccess) {
@@ -262,10 +266,47 @@ void rt_batch_destroy(rt_batch* b)
     if (b->d_samp) cudaFree(b->d_samp);
     if (b->d_pcnt) cudaFree(b->d_pcnt);
     if (b->d_br) cudaFree(b->d_br);
+    if (b->staged) { cudaEventSynchronize(b->staged); cudaEventDestroy(b->staged); }
+    if (b->h_stage) cudaFreeHost(b->h_stage);
     if (b->d_rgbs) cudaFree(b->d_rgbs);
     if (b->d_counters) cudaFree(b->d_counters);
     if (b->done) cudaEventDestroy(b->done);
     delete b;
+}
+
+int rt_batch_update(rt_batch* b, const rt_scene_desc* descs, int32_t n, void* stream, uint64_t* h2d_bytes)
+{
+    RT_REQ(b && descs, "batch and descs must not be NULL");
+    RT_REQ(n == b->n, "the batch holds %d scenes, got %d descriptors", b->n, n);
+    std::vector<DevScene> dev(n);
+    for (int i = 0; i < n; ++i) {
+        if (rt_validate_desc(&descs[i]) != RT_OK) return RT_EINVAL;
+        const DevScene& old = b->h_scenes[i];
+        build_scene_table(&descs[i], &dev[i]);
+        RT_REQ(descs[i].precision == b->precision && descs[i].integrator == b->integrator,
+               "scene %d: precision and integrator must stay", i);
+        RT_REQ(dev[i].nwork == old.nwork && dev[i].spp == old.spp && dev[i].wout == old.wout,
+               "scene %d: image size and samples per pixel must stay", i);
+        RT_REQ(dev[i].background == old.background && dev[i].flags == old.flags,
+               "scene %d: background kind and flags must stay", i);
+        dev[i].tex = old.tex;
+        dev[i].tex_size = old.tex_size;
+        dev[i].pix_list = nullptr;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t bytes = sizeof(DevScene) * (size_t)n;
+    if (!b->h_stage) {
+        RT_CK(cudaMallocHost((void**)&b->h_stage, bytes));
+        RT_CK(cudaEventCreateWithFlags(&b->staged, cudaEventDisableTiming));
+    } else {
+        RT_CK(cudaEventSynchronize(b->staged));     // the previous copy has left the staging buffer
+    }
+    memcpy(b->h_stage, dev.data(), bytes);
+    RT_CK(cudaMemcpyAsync(b->d_scenes, b->h_stage, bytes, cudaMemcpyHostToDevice, st));
+    RT_CK(cudaEventRecord(b->staged, st));
+    b->h_scenes = dev;
+    if (h2d_bytes) *h2d_bytes = bytes;
+    return RT_OK;
 }
 
 int rt_batch_render(rt_batch* b, float* const* d_rgb, void* stream)

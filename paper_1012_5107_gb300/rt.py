@@ -78,7 +78,7 @@ _lib = None
 EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels", "rt_render_host",
            "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_scene_autotune",
            "rt_batch_create", "rt_batch_destroy", "rt_batch_render", "rt_batch_stats", "rt_batch_set_launch",
-           "rt_batch_get_launch", "rt_batch_autotune",
+           "rt_batch_get_launch", "rt_batch_autotune", "rt_batch_update",
            "rt_validate_desc", "rt_request_bytes", "rt_server_create", "rt_server_destroy", "rt_submit", "rt_poll",
            "rt_server_stats",
            "rt_xcorr", "rt_xcorr_noalloc", "rt_xcorr_map", "rt_eval_medium", "rt_last_error", "rt_version"]
@@ -112,6 +112,7 @@ def lib() -> C.CDLL:
     L.rt_batch_set_launch.argtypes = [vp, C.c_int32]
     L.rt_batch_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int64)]
     L.rt_batch_autotune.argtypes = [vp, C.POINTER(vp), C.c_int32, vp, C.POINTER(C.c_int32)]
+    L.rt_batch_update.argtypes = [vp, C.POINTER(SceneDesc), C.c_int32, vp, C.POINTER(C.c_uint64)]
     L.rt_xcorr.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
                            C.c_double, vp, vp]
     L.rt_xcorr_noalloc.argtypes = [vp, vp, C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double), C.c_int32,
@@ -266,6 +267,17 @@ class Batch:
 
     def render(self, outs, stream=None):
         _check(lib().rt_batch_render(self._h, self._outs(outs), _stream(stream)))
+
+    def update(self, params: list, stream=None) -> int:
+        """New parameters for every scene (rt_batch_update): the table is copied
+        to the device on `stream` before the next render; returns the bytes copied."""
+        assert len(params) == len(self.scenes)
+        arr = (SceneDesc * len(params))()
+        for q, p in enumerate(params):
+            arr[q], _ = make_desc(p, None)
+        b = C.c_uint64()
+        _check(lib().rt_batch_update(self._h, arr, len(params), _stream(stream), C.byref(b)))
+        return b.value
 
     def stats(self) -> dict:
         s = Stats()

@@ -87,3 +87,28 @@ def test_batch_autotune(rt):
     outs = [torch.zeros(sc.shape, dtype=torch.float32, device="cuda") for sc in scenes]
     m = batch.autotune(outs, trials=1)
     assert 12 <= m <= 28 and batch.get_launch()["min_active"] == m
+
+
+def test_update_moves_the_camera(rt):
+    """rt_batch_update: a new camera and grating amplitude for the next frame
+    give the images of those scenes rendered alone."""
+    import torch
+    params = [inputs.base_scene(width=48, height=40, spp=2, seed=21 + q, scene_id=q, precision=0) for q in range(3)]
+    scenes = [rt.Scene(p) for p in params]
+    outs = [torch.zeros(sc.shape, dtype=torch.float32, device="cuda") for sc in scenes]
+    b = rt.Batch(scenes)
+    b.render(outs)
+    moved = [dict(p, elev_deg=35.0 + 5 * q, azim_deg=10.0 * q, A=0.03) for q, p in enumerate(params)]
+    nbytes = b.update(moved)
+    assert nbytes > 0
+    b.render(outs)
+    torch.cuda.synchronize()
+    for p, o in zip(moved, outs):
+        sc = rt.Scene(p)
+        ref = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+        sc.render(ref)
+        torch.cuda.synchronize()
+        assert torch.equal(o, ref)
+    with pytest.raises(rt.RtError):
+        b.update([dict(params[0], width=64)] + moved[1:])      # image size must stay
+    b.close()

@@ -84,6 +84,11 @@ template <> struct Mth<float> {
         asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
         return y;
     }
+    static __device__ __forceinline__ float lg2(float x) {
+        float y;
+        asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+        return y;
+    }
     // sin and cos of 2 pi a for |a| <= 1/2
     static __device__ __forceinline__ void sincos2pi(float a, float& s, float& c) {
         __sincosf(6.28318530717958647692f * a, &s, &c);

@@ -299,74 +299,141 @@ struct DPT {
                             e6 = 11.0 / 84 - 187.0 / 2100, e7 = -1.0 / 40;
 };
 
+// The tableau as a function: a(j, k) for stages j, k = 1..7, row 7 holding
+// the fifth-order weights b (first same as last), and e(j) = b_j - b*_j.
+__host__ __device__ constexpr double dp_a(int j, int k)
+{
+    return j == 2 ? (k == 1 ? DPT::a21 : 0.0)
+         : j == 3 ? (k == 1 ? DPT::a31 : k == 2 ? DPT::a32 : 0.0)
+         : j == 4 ? (k == 1 ? DPT::a41 : k == 2 ? DPT::a42 : k == 3 ? DPT::a43 : 0.0)
+         : j == 5 ? (k == 1 ? DPT::a51 : k == 2 ? DPT::a52 : k == 3 ? DPT::a53 : k == 4 ? DPT::a54 : 0.0)
+         : j == 6 ? (k == 1 ? DPT::a61 : k == 2 ? DPT::a62 : k == 3 ? DPT::a63 : k == 4 ? DPT::a64
+                     : k == 5 ? DPT::a65 : 0.0)
+         : j == 7 ? (k == 1 ? DPT::b1 : k == 3 ? DPT::b3 : k == 4 ? DPT::b4 : k == 5 ? DPT::b5
+                     : k == 6 ? DPT::b6 : 0.0)
+         : 0.0;
+}
+__host__ __device__ constexpr double dp_e(int j)
+{
+    return j == 1 ? DPT::e1 : j == 3 ? DPT::e3 : j == 4 ? DPT::e4 : j == 5 ? DPT::e5 : j == 6 ? DPT::e6
+         : j == 7 ? DPT::e7 : 0.0;
+}
+// Nystrom form for r'' = F(r): node c_j = sum_k a_jk, position weights
+// (A A)_jl = sum_k a_jk a_kl of the forces, and (e A)_l = sum_j e_j a_jl.
+__host__ __device__ constexpr double dp_c(int j)
+{
+    double c = 0.0;
+    for (int k = 1; k < j; ++k) c += dp_a(j, k);
+    return c;
+}
+__host__ __device__ constexpr double dp_aa(int j, int l)
+{
+    double v = 0.0;
+    for (int k = l + 1; k < j; ++k) v += dp_a(j, k) * dp_a(k, l);
+    return v;
+}
+__host__ __device__ constexpr double dp_ea(int l)
+{
+    double v = 0.0;
+    for (int j = l + 1; j <= 7; ++j) v += dp_e(j) * dp_a(j, l);
+    return v;
+}
+
+// Coefficients of the Nystrom form for the stage loop: row j - 2 of kDpAA
+// holds (A A)_jl for stages j = 2..6 and (b A)_l for the solution (j = 7);
+// kDpC the nodes c_j.  The loop over the stages is kept rolled, with one
+// evaluation of W0 and the force in its body: unrolled, the seven inlined
+// evaluations overflow the instruction cache (most issue slots were lost to
+// instruction fetch).
+#define RT_DPAA_ROW(j) \
+    {(float)dp_aa(j, 1), (float)dp_aa(j, 2), (float)dp_aa(j, 3), (float)dp_aa(j, 4), (float)dp_aa(j, 5), (float)dp_aa(j, 6)}
+#define RT_DPAA_ROWD(j) {dp_aa(j, 1), dp_aa(j, 2), dp_aa(j, 3), dp_aa(j, 4), dp_aa(j, 5), dp_aa(j, 6)}
+static __constant__ float kDpAAf[6][6] = {RT_DPAA_ROW(2), RT_DPAA_ROW(3), RT_DPAA_ROW(4),
+                                          RT_DPAA_ROW(5), RT_DPAA_ROW(6), RT_DPAA_ROW(7)};
+static __constant__ double kDpAAd[6][6] = {RT_DPAA_ROWD(2), RT_DPAA_ROWD(3), RT_DPAA_ROWD(4),
+                                           RT_DPAA_ROWD(5), RT_DPAA_ROWD(6), RT_DPAA_ROWD(7)};
+#undef RT_DPAA_ROW
+#undef RT_DPAA_ROWD
+static __constant__ float kDpCf[6] = {(float)dp_c(2), (float)dp_c(3), (float)dp_c(4), (float)dp_c(5), (float)dp_c(6), 1.0f};
+static __constant__ double kDpCd[6] = {dp_c(2), dp_c(3), dp_c(4), dp_c(5), dp_c(6), 1.0};
+template <class R> __device__ __forceinline__ R dp_tab_aa(int r, int c);
+template <> __device__ __forceinline__ float dp_tab_aa<float>(int r, int c) { return kDpAAf[r][c]; }
+template <> __device__ __forceinline__ double dp_tab_aa<double>(int r, int c) { return kDpAAd[r][c]; }
+template <class R> __device__ __forceinline__ R dp_tab_c(int r);
+template <> __device__ __forceinline__ float dp_tab_c<float>(int r) { return kDpCf[r]; }
+template <> __device__ __forceinline__ double dp_tab_c<double>(int r) { return kDpCd[r]; }
+
 // One Dormand-Prince step of size h from s (W0 solved and force known at s)
 // into o: the fifth-order solution, W0 solved and the force at it (the first
 // stage of the next step).  e[4] receives the error estimate of
-// (x, y, p_x, p_y).  The ODE is r' = p, p' = F(r): a stage momentum is
-// p + h sum a F and a stage position r + h sum a p_stage.
+// (x, y, p_x, p_y).  The ODE is r' = p, p' = F(r) with F a function of r
+// alone, so the method is taken in its Nystrom form: stage momenta
+// p + h sum_k a_jk F_k are never needed, stage positions are
+// r + c_j h p + h^2 sum_l (A A)_jl F_l, the solution
+// r + h p + h^2 sum_l (b A)_l F_l and p + h sum_j b_j F_j, and the position
+// error h^2 sum_l (e A)_l F_l -- the same method with only the forces kept.
 template <class R>
 __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
                                           LaneStats& st)
 {
-    typedef DPT T;
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     R Xp = s.X, yp = s.y;
-    const R F1x = s.Fx, F1y = s.Fy, P1x = s.px, P1y = s.py;
-    auto stage = [&](R Px, R Py, R dXs, R dYs, R& Fx, R& Fy) {
-        const R Xs = s.X + dXs, Ys = s.y + dYs;
+    const R hpx = h * s.px, hpy = h * s.py, hh = h * h;
+    R Fx[7], Fy[7];
+    Fx[0] = s.Fx;
+    Fy[0] = s.Fy;
+#pragma unroll 1
+    for (int j = 2; j <= 7; ++j) {
+        R ax = R(0), ay = R(0);
+        const int nl = (j < 7) ? j - 2 : 6;
+#pragma unroll 1
+        for (int l = 0; l < nl; ++l) {
+            const R a = dp_tab_aa<R>(j - 2, l);
+            ax += a * Fx[l];
+            ay += a * Fy[l];
+        }
+        R Xs, Ys;
+        if (j < 7) {
+            Xs = s.X + (dp_tab_c<R>(j - 2) * hpx + hh * ax);
+            Ys = s.y + (dp_tab_c<R>(j - 2) * hpy + hh * ay);
+        } else {
+            R fx = R(0), fy = R(0);
+#pragma unroll
+            for (int l = 1; l <= 6; ++l) {
+                fx += R(dp_a(7, l)) * Fx[l - 1];
+                fy += R(dp_a(7, l)) * Fy[l - 1];
+            }
+            o = s;
+            kahan_add(o.X, o.cX, hpx + hh * ax);
+            kahan_add(o.y, o.cy, hpy + hh * ay);
+            kahan_add(o.z, o.cz, h * s.pz);
+            kahan_add(o.px, o.cpx, h * fx);
+            kahan_add(o.py, o.cpy, h * fy);
+            Xs = o.X;
+            Ys = o.y;
+        }
         w0_continue(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, st);
-        ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+        ray_force(wr, wi, rr, ri, k.fk, Fx[j - 1], Fy[j - 1]);
         Xp = Xs;
         yp = Ys;
-    };
-    // stage 2
-    const R P2x = P1x + h * R(T::a21) * F1x, P2y = P1y + h * R(T::a21) * F1y;
-    R F2x, F2y;
-    stage(P2x, P2y, h * R(T::a21) * P1x, h * R(T::a21) * P1y, F2x, F2y);
-    // stage 3
-    const R P3x = P1x + h * (R(T::a31) * F1x + R(T::a32) * F2x), P3y = P1y + h * (R(T::a31) * F1y + R(T::a32) * F2y);
-    R F3x, F3y;
-    stage(P3x, P3y, h * (R(T::a31) * P1x + R(T::a32) * P2x), h * (R(T::a31) * P1y + R(T::a32) * P2y), F3x, F3y);
-    // stage 4
-    const R P4x = P1x + h * (R(T::a41) * F1x + R(T::a42) * F2x + R(T::a43) * F3x);
-    const R P4y = P1y + h * (R(T::a41) * F1y + R(T::a42) * F2y + R(T::a43) * F3y);
-    R F4x, F4y;
-    stage(P4x, P4y, h * (R(T::a41) * P1x + R(T::a42) * P2x + R(T::a43) * P3x),
-          h * (R(T::a41) * P1y + R(T::a42) * P2y + R(T::a43) * P3y), F4x, F4y);
-    // stage 5
-    const R P5x = P1x + h * (R(T::a51) * F1x + R(T::a52) * F2x + R(T::a53) * F3x + R(T::a54) * F4x);
-    const R P5y = P1y + h * (R(T::a51) * F1y + R(T::a52) * F2y + R(T::a53) * F3y + R(T::a54) * F4y);
-    R F5x, F5y;
-    stage(P5x, P5y, h * (R(T::a51) * P1x + R(T::a52) * P2x + R(T::a53) * P3x + R(T::a54) * P4x),
-          h * (R(T::a51) * P1y + R(T::a52) * P2y + R(T::a53) * P3y + R(T::a54) * P4y), F5x, F5y);
-    // stage 6
-    const R P6x = P1x + h * (R(T::a61) * F1x + R(T::a62) * F2x + R(T::a63) * F3x + R(T::a64) * F4x + R(T::a65) * F5x);
-    const R P6y = P1y + h * (R(T::a61) * F1y + R(T::a62) * F2y + R(T::a63) * F3y + R(T::a64) * F4y + R(T::a65) * F5y);
-    R F6x, F6y;
-    stage(P6x, P6y,
-          h * (R(T::a61) * P1x + R(T::a62) * P2x + R(T::a63) * P3x + R(T::a64) * P4x + R(T::a65) * P5x),
-          h * (R(T::a61) * P1y + R(T::a62) * P2y + R(T::a63) * P3y + R(T::a64) * P4y + R(T::a65) * P5y), F6x, F6y);
-    // fifth-order solution
-    const R dX = h * (R(T::b1) * P1x + R(T::b3) * P3x + R(T::b4) * P4x + R(T::b5) * P5x + R(T::b6) * P6x);
-    const R dY = h * (R(T::b1) * P1y + R(T::b3) * P3y + R(T::b4) * P4y + R(T::b5) * P5y + R(T::b6) * P6y);
-    const R dPx = h * (R(T::b1) * F1x + R(T::b3) * F3x + R(T::b4) * F4x + R(T::b5) * F5x + R(T::b6) * F6x);
-    const R dPy = h * (R(T::b1) * F1y + R(T::b3) * F3y + R(T::b4) * F4y + R(T::b5) * F5y + R(T::b6) * F6y);
-    const R P7x = s.px + dPx, P7y = s.py + dPy;
-    o = s;
-    kahan_add(o.X, o.cX, dX);
-    kahan_add(o.y, o.cy, dY);
-    kahan_add(o.z, o.cz, h * s.pz);
-    kahan_add(o.px, o.cpx, dPx);
-    kahan_add(o.py, o.cpy, dPy);
-    // force at the fifth-order point (first same as last)
-    w0_continue(k, o.X, o.y, o.X - Xp, o.y - yp, wr, wi, rr, ri, st);
+    }
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
-    ray_force(wr, wi, rr, ri, k.fk, o.Fx, o.Fy);
-    // error estimate h sum (b - b*) k over the seven stages
-    e[0] = h * (R(T::e1) * P1x + R(T::e3) * P3x + R(T::e4) * P4x + R(T::e5) * P5x + R(T::e6) * P6x + R(T::e7) * P7x);
-    e[1] = h * (R(T::e1) * P1y + R(T::e3) * P3y + R(T::e4) * P4y + R(T::e5) * P5y + R(T::e6) * P6y + R(T::e7) * P7y);
-    e[2] = h * (R(T::e1) * F1x + R(T::e3) * F3x + R(T::e4) * F4x + R(T::e5) * F5x + R(T::e6) * F6x + R(T::e7) * o.Fx);
-    e[3] = h * (R(T::e1) * F1y + R(T::e3) * F3y + R(T::e4) * F4y + R(T::e5) * F5y + R(T::e6) * F6y + R(T::e7) * o.Fy);
+    o.Fx = Fx[6];
+    o.Fy = Fy[6];
+    R ex = R(0), ey = R(0), gx = R(0), gy = R(0);
+#pragma unroll
+    for (int l = 1; l <= 7; ++l) {
+        if (l <= 6) {
+            ex += R(dp_ea(l)) * Fx[l - 1];
+            ey += R(dp_ea(l)) * Fy[l - 1];
+        }
+        gx += R(dp_e(l)) * Fx[l - 1];
+        gy += R(dp_e(l)) * Fy[l - 1];
+    }
+    e[0] = hh * ex;
+    e[1] = hh * ey;
+    e[2] = h * gx;
+    e[3] = h * gy;
     if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
     else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
 }
@@ -1093,9 +1160,20 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         const R scp = k.atol + k.rtol;                                    // positions (units of Lambda)
         const R s2 = k.atol + k.rtol * fmax(fabs(s.px), fabs(o.px));
         const R s3 = k.atol + k.rtol * fmax(fabs(s.py), fabs(o.py));
-        const R q0 = e[0] / scp, q1 = e[1] / scp, q2 = e[2] / s2, q3 = e[3] / s3;
-        const R err = Mth<R>::sqrt_(R(0.25) * (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3));
-        R fac = (err > R(0)) ? R(0.9) * pow(err, R(-0.2)) : R(5);
+        R err, fac;
+        if constexpr (sizeof(R) == 4) {
+            // FP32: reciprocals and err^-1/5 = (err^2)^-1/10 on the MUFU pipe
+            // (the step factor is a heuristic; a few ulp do not matter)
+            const R iscp = Mth<R>::rcp(scp);
+            const R q0 = e[0] * iscp, q1 = e[1] * iscp, q2 = e[2] * Mth<R>::rcp(s2), q3 = e[3] * Mth<R>::rcp(s3);
+            const R err2 = R(0.25) * (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3);
+            err = err2;                                                   // err <= 1 iff err^2 <= 1
+            fac = (err2 > R(0)) ? R(0.9) * Mth<R>::ex2(R(-0.1) * Mth<R>::lg2(err2)) : R(5);
+        } else {
+            const R q0 = e[0] / scp, q1 = e[1] / scp, q2 = e[2] / s2, q3 = e[3] / s3;
+            err = Mth<R>::sqrt_(R(0.25) * (q0 * q0 + q1 * q1 + q2 * q2 + q3 * q3));
+            fac = (err > R(0)) ? R(0.9) * pow(err, R(-0.2)) : R(5);
+        }
         fac = fmin(R(5), fmax(R(0.2), fac));
         if (!(err <= R(1))) {
             if (!isfinite(err)) {

@@ -290,6 +290,9 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
             }
             const int64_t max_steps = sc.max_steps;
             for (int it = 0; it < kWaveTaskSteps; ++it) {
+#if RT_PROFILE
+                prof[2] += 1;
+#endif
                 if (phase == PH_BOX) box_step<R, INTEG>(*kp, max_steps, C, b, phase, surf, steps, st);
                 if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
             }

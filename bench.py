@@ -327,6 +327,7 @@ def run_gpu(args):
 
     xmap = bench_xcorr_map(rt, torch, step, stream, clock_mhz)
     table1 = None if args.no_table1 else bench_table1(rt, torch, stream)
+    hd = None if args.no_hd else bench_hd(rt, torch, stream)
     batch = None if args.no_batch else bench_batch(rt, torch, stream)
     serving = None if args.no_serving else bench_serving(rt, torch)
 
@@ -354,6 +355,7 @@ def run_gpu(args):
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "xcorr_map": xmap,
         "table1_referenced_fresnel": table1,
+        "hd_dp45_1920x1080x16": hd,
         "batched_64_scenes": batch,
         "serving": serving,
         "gpu_launches": step.launches * args.steps,
@@ -440,6 +442,37 @@ def bench_table1(rt, torch, stream) -> dict:
             row[f"C_cloak_vs_{ref}"] = {"0": round(float(cl[0, 3]), 4), "10": round(float(cf[0, 3]), 4),
                                         "25": round(float(cf[1, 3]), 4), "50": round(float(cf[2, 3]), 4)}
         out[f"H={H}"] = row
+    return out
+
+
+def bench_hd(rt, torch, stream) -> dict:
+    """The 1920 x 1080, 16 samples per pixel workload with adaptive
+    Dormand-Prince (rtol = atol = 1e-5, FP32) and the seeded 2048^2
+    value-noise background, over the cloak extents E = 2, 4, 8, 16, 32 Lambda
+    and amplitudes A = 0.02, 0.04: one full render each, timed."""
+    tex = inputs.value_noise(2048, seed=3)
+    out = {}
+    total_rays, total_ms, total_steps = 0, 0.0, 0
+    for A in (0.02, 0.04):
+        for E in (2.0, 4.0, 8.0, 16.0, 32.0):
+            sc = rt.Scene(inputs.config_hd(extent=E, A=A, precision=inputs.FP32), tex=tex)
+            img = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+            with torch.cuda.stream(stream):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                sc.render(img, stream=stream)
+                e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            st = sc.stats()
+            out[f"E={E:g},A={A:g}"] = {"ms": round(ms, 2), "Mrays_per_s": round(st["rays"] / ms / 1e3, 2),
+                                      "steps_per_ray": round(st["steps"] / st["rays"], 1)}
+            total_rays += st["rays"]
+            total_ms += ms
+            total_steps += st["steps"]
+            sc.close()
+    out["all"] = {"renders": 10, "ms": round(total_ms, 1), "Mrays_per_s": round(total_rays / total_ms / 1e3, 2),
+                  "Gsteps_per_s": round(total_steps / total_ms / 1e6, 2)}
     return out
 
 
@@ -579,6 +612,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-table1", action="store_true")
+    ap.add_argument("--no-hd", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -18,6 +18,8 @@
  *   - the ray ODE is integrated in the Hamiltonian parameter tau,
  *     dr/dtau = p, dp/dtau = grad(n^2)/2 = n grad n, |p| = n, which traces
  *     the same curves as the Newtonian form of Eq. 11 (dtau = c0/n^2 dt);
+ *     integrator 2 integrates Eq. 11 itself in physical time t (c0 = 1,
+ *     state (r, v), |v| = 1/n) with classical RK4 of fixed step h in t;
  *   - W0 is evaluated by Halley's iteration, cold-started at every call;
  *   - the grating hit inside the cloak is the root theta in (0,1] of
  *     v(Phi_{theta h}(s)) = 0 with v = Im w = y + Re(W0)/k, where Phi is one
@@ -196,6 +198,14 @@ static void or_rhs(const or_scene* sc, const double s[6], double ds[6], counters
     double n, gn[3];
     or_medium(sc, s[0], s[1], &W, &n, gn, cnt);
     ds[0] = s[3]; ds[1] = s[4]; ds[2] = s[5];
+    if (sc->integrator == 2) {
+        /* Eq. 11 in physical time t (c0 = 1): the state is (r, v), |v| = 1/n,
+           dv/dt = (|v|^2 grad n - 2 (grad n . v) v) / n */
+        const double v2 = s[3] * s[3] + s[4] * s[4] + s[5] * s[5];
+        const double gv = gn[0] * s[3] + gn[1] * s[4] + gn[2] * s[5];
+        for (int a = 0; a < 3; ++a) ds[3 + a] = (v2 * gn[a] - 2.0 * gv * s[3 + a]) / n;
+        return;
+    }
     ds[3] = n * gn[0]; ds[4] = n * gn[1]; ds[5] = n * gn[2];
 }
 
@@ -525,7 +535,7 @@ typedef struct step_ctx {
 
 static void or_partial_step(step_ctx* c, double theta, double out[6])
 {
-    if (c->sc->integrator == 0) {
+    if (c->sc->integrator != 1) {
         or_rk4(c->sc, c->s, theta * c->h, out, c->cnt);
     } else {
         double y4[6], k7[6];
@@ -846,8 +856,16 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
             continue;
         }
 
-        /* Inside the cloak: integrate the ray ODE step by step. */
+        /* Inside the cloak: integrate the ray ODE step by step.  p is the
+           momentum (|p| = n); the time form of Eq. 11 (integrator 2) carries
+           the velocity v = p / n^2 (|v| = c0 / n with c0 = 1) instead. */
         double s[6] = {X[0], X[1], X[2], p[0], p[1], p[2]};
+        if (sc->integrator == 2) {
+            double complex W;
+            double n, gn[3];
+            or_medium(sc, X[0], X[1], &W, &n, gn, &cnt);
+            for (int a = 0; a < 3; ++a) s[3 + a] = p[a] / (n * n);
+        }
         double k1[6], k7[6];
         double h = sc->h;
         int have_k1 = 0;
@@ -858,7 +876,7 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
             if (bounces > sc->max_bounces) { status = ST_MAX_BOUNCES; break; }
             double s1[6];
             double hs = h;
-            if (sc->integrator == 0) {
+            if (sc->integrator != 1) {
                 or_rk4(sc, s, hs, s1, &cnt);
                 steps++;
             } else {
@@ -930,15 +948,25 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
                 traj_push(tb, s);
                 continue;
             }
-            /* a face of the box: refract into air or reflect totally */
+            /* a face of the box: refract into air or reflect totally, acting
+               on the momentum (p = n^2 v in the time form) */
             double Nf[3];
             or_face_normal(ev_best, Nf);
-            const double pn = s[3] * Nf[0] + s[4] * Nf[1] + s[5] * Nf[2];
+            double pm[3] = {s[3], s[4], s[5]};
+            double n2f = 1.0;
+            if (sc->integrator == 2) {
+                double complex W;
+                double nf, gn[3];
+                or_medium(sc, s[0], s[1], &W, &nf, gn, &cnt);
+                n2f = nf * nf;
+                for (int a = 0; a < 3; ++a) pm[a] *= n2f;
+            }
+            const double pn = pm[0] * Nf[0] + pm[1] * Nf[1] + pm[2] * Nf[2];
             double pt[3];
-            for (int a = 0; a < 3; ++a) pt[a] = s[3 + a] - pn * Nf[a];
+            for (int a = 0; a < 3; ++a) pt[a] = pm[a] - pn * Nf[a];
             const double pt2 = or_dot(pt, pt);
             if (pt2 >= 1.0) {
-                for (int a = 0; a < 3; ++a) s[3 + a] -= 2.0 * pn * Nf[a];
+                for (int a = 0; a < 3; ++a) s[3 + a] -= 2.0 * (pn / n2f) * Nf[a];
                 bounces++;
                 surface = ev_best;
                 traj_push(tb, s);
@@ -946,10 +974,10 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
             }
             const double pn_out = sqrt(1.0 - pt2);
             if (fresnel) {
-                const double n1 = sqrt(s[3] * s[3] + s[4] * s[4] + s[5] * s[5]);   /* |p| = n */
+                const double n1 = sqrt(or_dot(pm, pm));                          /* |p| = n */
                 const double R = or_fresnel_R(n1, 1.0, pn, pn_out);
                 double pr[3];
-                for (int a = 0; a < 3; ++a) pr[a] = s[3 + a] - 2.0 * pn * Nf[a];
+                for (int a = 0; a < 3; ++a) pr[a] = pm[a] - 2.0 * pn * Nf[a];
                 or_push_branch(br, nbr, s, pr, w * R, MED_BOX, ev_best, bounces, events, steps);
                 w *= 1.0 - R;
             }

@@ -135,3 +135,43 @@ def test_rk4_converges_and_agrees_with_dp45(orc):
     assert e1 / max(e2, 1e-300) > 8.0          # ~ (2^4 - 1)/(1 - 2^-4) * ... for fourth order
     assert np.abs(dirs["h4"]["dir"] - dirs["dp"]["dir"])[ok].max() < 1e-7
     assert np.abs(dirs["h4"]["pos"] - dirs["dp"]["pos"])[ok].max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# The tracer's time form of Eq. 11 (integrator 2: RK4 in t, state (r, v))
+# ---------------------------------------------------------------------------
+def test_time_form_tracer_matches_tau_form(orc):
+    """A ray started inside the cloak leaves at the same point in the same
+    direction whether the tracer integrates Eq. 11 in t or the Hamiltonian
+    form in tau (the same curves, Sec. 3); the step sizes differ, so they
+    agree to the integration error."""
+    from paper_1012_5107_gb300 import inputs
+    base = inputs.base_scene(A=0.05, h=1.0 / 800, precision=1)
+    tau = orc.Scene(base)
+    tform = orc.Scene(dict(base, integrator=2))
+    X = np.array([0.21, 0.9, -0.3])
+    d = np.array([0.3, -0.85, 0.12]); d /= np.linalg.norm(d)
+    n0 = orc.index(tau, X[0], X[1])[2]
+    ra, _ = orc.trace_from(tau, X, n0 * d, medium=1)
+    rb, _ = orc.trace_from(tform, X, n0 * d, medium=1)
+    assert ra["bounces"] == rb["bounces"] >= 1 and ra["status"] == rb["status"]
+    assert np.abs(ra["pos"] - rb["pos"]).max() < 1e-9
+    assert np.abs(ra["dir"] - rb["dir"]).max() < 1e-9
+
+
+def test_time_form_invariants(orc):
+    """Along the time-form solution the speed stays c0/n and n^2 v_z (the
+    conserved momentum p_z of the z-translation invariance) stays fixed."""
+    from paper_1012_5107_gb300 import inputs
+    sc = orc.Scene(inputs.base_scene(A=0.05, h=1.0 / 400, integrator=2, precision=1))
+    X = np.array([-0.37, 1.1, 0.2])
+    d = np.array([0.2, -0.9, 0.35]); d /= np.linalg.norm(d)
+    n0 = orc.index(sc, X[0], X[1])[2]
+    _, traj = orc.trace_from(sc, X, n0 * d, medium=1, traj_cap=20000)
+    assert len(traj) > 100
+    seg = traj[: np.argmax(np.abs(np.diff(traj[:, 4])) > 0.05)]     # up to the first reflection
+    n = orc.index(sc, seg[:, 0], seg[:, 1])[:, 2]
+    speed = np.linalg.norm(seg[:, 3:], axis=1)
+    assert np.abs(speed * n - 1.0).max() < 1e-10
+    pz = n * n * seg[:, 5]
+    assert np.abs(pz - pz[0]).max() < 1e-10

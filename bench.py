@@ -328,6 +328,7 @@ def run_gpu(args):
     xmap = bench_xcorr_map(rt, torch, step, stream, clock_mhz)
     table1 = None if args.no_table1 else bench_table1(rt, torch, stream)
     hd = None if args.no_hd else bench_hd(rt, torch, stream)
+    tform = None if args.no_time_form else bench_time_form(rt, torch, stream)
     batch = None if args.no_batch else bench_batch(rt, torch, stream)
     serving = None if args.no_serving else bench_serving(rt, torch)
 
@@ -356,6 +357,7 @@ def run_gpu(args):
         "xcorr_map": xmap,
         "table1_referenced_fresnel": table1,
         "hd_dp45_1920x1080x16": hd,
+        "time_form_eq11_cloak_render": tform,
         "batched_64_scenes": batch,
         "serving": serving,
         "gpu_launches": step.launches * args.steps,
@@ -473,6 +475,34 @@ def bench_hd(rt, torch, stream) -> dict:
             sc.close()
     out["all"] = {"renders": 10, "ms": round(total_ms, 1), "Mrays_per_s": round(total_rays / total_ms / 1e3, 2),
                   "Gsteps_per_s": round(total_steps / total_ms / 1e6, 2)}
+    return out
+
+
+def bench_time_form(rt, torch, stream) -> dict:
+    """The cloaked 512 x 512 x 4 render with the time form of Eq. 11 (RK4 on
+    (r, v) in physical time, step Lambda/200 in t): FP32 over five launches
+    and FP64 over one, each after a warm-up launch."""
+    out = {}
+    for name, prec, n in (("fp32", inputs.FP32, 5), ("fp64", inputs.FP64, 1)):
+        p = dict(inputs.three_renders(inputs.config_main(precision=prec))["cloak"], integrator=2)
+        sc = rt.Scene(p)
+        img = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+        with torch.cuda.stream(stream):
+            sc.render(img, stream=stream)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            e0.record(stream)
+            for _ in range(n):
+                sc.render(img, stream=stream)
+            e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / n
+        st = sc.stats()
+        out[name] = {"cloak_ms": round(ms, 3), "Mrays_per_s": round(st["rays"] / (ms * 1e-3) / 1e6, 3),
+                     "Gsteps_per_s": round(st["steps"] / (ms * 1e-3) / 1e9, 4),
+                     "steps_per_ray": round(st["steps"] / st["rays"], 1)}
+        sc.close()
     return out
 
 
@@ -613,6 +643,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-table1", action="store_true")
     ap.add_argument("--no-hd", action="store_true")
+    ap.add_argument("--no-time-form", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -61,6 +61,9 @@ extern "C" {
 #define RT_BG_TEXTURE 1       /* greyscale texture, bilinear, wrapping         */
 #define RT_RK4 0              /* classical Runge-Kutta, fixed step h           */
 #define RT_DP45 1             /* Dormand-Prince 5(4), adaptive (rtol, atol)    */
+#define RT_RK4T 2             /* classical Runge-Kutta on Eq. 11 in physical
+                                 time t (state r, v with |v| = c0/n), fixed
+                                 step h in t; wavefront loop only              */
 #define RT_FP32 0             /* single precision bulk arithmetic              */
 #define RT_FP64 1             /* double precision throughout                   */
 
@@ -125,7 +128,7 @@ typedef struct rt_scene_desc {
                                  (height x 1 image, horizontal offset 0)        */
     int32_t background;       /* RT_BG_*                                        */
     int32_t tex_size;         /* texture side                                   */
-    int32_t integrator;       /* RT_RK4 | RT_DP45                               */
+    int32_t integrator;       /* RT_RK4 | RT_DP45 | RT_RK4T                     */
     int32_t precision;        /* RT_FP32 | RT_FP64                              */
     int32_t max_bounces;      /* guard on reflections per ray                   */
     int32_t flags;            /* RT_FLAG_* (0: the plain method)                */
@@ -215,7 +218,8 @@ int rt_scene_stats(rt_scene* scene, rt_stats* out);
  *               4, 5, 6 resident blocks of 128 threads per SM (1 and 2 for
  *               FP32 RK4 only); 3: the wavefront loop (a pool of pixels in
  *               flight per block, rays inside the cloak regrouped into full
- *               warps); -1 keeps the current one
+ *               warps; the only one for RT_RK4T and for scenes with
+ *               flags); -1 keeps the current one
  *   min_active  the integration loop of a warp continues while at least this
  *               many of its 32 lanes are inside the cloak (1..32); 0 keeps it
  * Returns RT_EINVAL for values out of range or a variant not compiled for the

@@ -98,7 +98,8 @@ static int validate(const rt_scene_desc* d)
     RT_REQ(d->elev_deg >= -90.0 && d->elev_deg <= 90.0 && std::fabs(std::cos(d->elev_deg * kPi / 180.0)) > 1e-9,
            "elev_deg must be in (-90, 90)");
     RT_REQ(std::isfinite(d->azim_deg), "azim_deg must be finite");
-    RT_REQ(d->integrator == RT_RK4 || d->integrator == RT_DP45, "integrator must be RT_RK4 or RT_DP45");
+    RT_REQ(d->integrator == RT_RK4 || d->integrator == RT_DP45 || d->integrator == RT_RK4T,
+           "integrator must be RT_RK4, RT_DP45 or RT_RK4T");
     RT_REQ(d->precision == RT_FP32 || d->precision == RT_FP64, "precision must be RT_FP32 or RT_FP64");
     RT_REQ(d->h > 0.0 && std::isfinite(d->h), "h must be > 0");
     if (d->integrator == RT_DP45)
@@ -184,6 +185,8 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->plate_n = 1.0 + s->kA;
     s->cd.fk = kTwoPi * s->idx_scale * s->idx_scale;
     s->cf.fk = (float)s->cd.fk;
+    s->cd.is2 = 1.0 / (s->idx_scale * s->idx_scale);
+    s->cf.is2 = (float)s->cd.is2;
     s->cd.ybot = (d->flags & RT_FLAG_PLATE) ? 0.0 : -s->A;
     s->cf.ybot = (float)s->cd.ybot;
     for (int a = 0; a < 3; ++a) {

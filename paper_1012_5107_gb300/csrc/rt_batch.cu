@@ -45,11 +45,14 @@ static cudaError_t batch_occupancy_t(int* bps)
 template <bool OPT>
 static cudaError_t batch_occupancy_o(int precision, int integrator, int* bps)
 {
-    if (precision == RT_FP64)
-        return integrator == RT_DP45 ? batch_occupancy_t<double, RT_DP45, OPT>(bps)
-                                     : batch_occupancy_t<double, RT_RK4, OPT>(bps);
-    return integrator == RT_DP45 ? batch_occupancy_t<float, RT_DP45, OPT>(bps)
-                                 : batch_occupancy_t<float, RT_RK4, OPT>(bps);
+    if (precision == RT_FP64) {
+        if (integrator == RT_DP45) return batch_occupancy_t<double, RT_DP45, OPT>(bps);
+        if (integrator == RT_RK4T) return batch_occupancy_t<double, RT_RK4T, OPT>(bps);
+        return batch_occupancy_t<double, RT_RK4, OPT>(bps);
+    }
+    if (integrator == RT_DP45) return batch_occupancy_t<float, RT_DP45, OPT>(bps);
+    if (integrator == RT_RK4T) return batch_occupancy_t<float, RT_RK4T, OPT>(bps);
+    return batch_occupancy_t<float, RT_RK4, OPT>(bps);
 }
 
 cudaError_t batch_occupancy(int precision, int integrator, bool opt, int* bps)
@@ -72,11 +75,14 @@ static cudaError_t launch_batch_t(const BatchLaunch& L, cudaStream_t stream)
 template <bool OPT>
 static cudaError_t launch_batch_o(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream)
 {
-    if (precision == RT_FP64)
-        return integrator == RT_DP45 ? launch_batch_t<double, RT_DP45, OPT>(L, stream)
-                                     : launch_batch_t<double, RT_RK4, OPT>(L, stream);
-    return integrator == RT_DP45 ? launch_batch_t<float, RT_DP45, OPT>(L, stream)
-                                 : launch_batch_t<float, RT_RK4, OPT>(L, stream);
+    if (precision == RT_FP64) {
+        if (integrator == RT_DP45) return launch_batch_t<double, RT_DP45, OPT>(L, stream);
+        if (integrator == RT_RK4T) return launch_batch_t<double, RT_RK4T, OPT>(L, stream);
+        return launch_batch_t<double, RT_RK4, OPT>(L, stream);
+    }
+    if (integrator == RT_DP45) return launch_batch_t<float, RT_DP45, OPT>(L, stream);
+    if (integrator == RT_RK4T) return launch_batch_t<float, RT_RK4T, OPT>(L, stream);
+    return launch_batch_t<float, RT_RK4, OPT>(L, stream);
 }
 
 cudaError_t launch_batch(int precision, int integrator, const BatchLaunch& L, cudaStream_t stream)

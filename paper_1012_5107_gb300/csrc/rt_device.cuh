@@ -30,6 +30,7 @@ struct StepConst {
     R w0tol;     // FP32: Newton on W0 stops when |dW|^2 <= w0tol
     R fk;        // force factor k s^2 (s: index scale of the cloak, 1 unless referenced)
     R ybot;      // bottom of the box: -A (cloak) or 0 (plate on the flat mirror)
+    R is2;       // 1/s^2: the time form's acceleration F/n^2 with F scaled by s^2 and n^2 = s^2 |r|^2
 };
 
 // Constants of the straight segments to the background, in the path's precision.

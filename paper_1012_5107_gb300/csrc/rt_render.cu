@@ -30,7 +30,8 @@ static cudaError_t wave_prepare()
 
 // Register-budget variants of the per-lane loop are compiled for the FP32 RK4
 // kernel, the one the benchmark times; the other (precision, integrator)
-// pairs have one each.  Every pair has the wavefront loop.
+// pairs have one each, but for the time form (RT_RK4T), which has none.
+// Every pair has the wavefront loop.
 template <class R, int INTEG>
 static cudaError_t occupancy_t(int variant, bool opt, int* bps)
 {
@@ -46,6 +47,9 @@ static cudaError_t occupancy_t(int variant, bool opt, int* bps)
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, false>, kWaveBlock,
                                                              wave_smem_bytes<R>());
     }
+    if constexpr (INTEG == RT_RK4T) {
+        return cudaErrorInvalidValue;                // the time form runs in the wavefront loop only
+    } else {
     if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
         if (variant == 1)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[1], INTEG>, kRenderBlock, 0);
@@ -53,6 +57,7 @@ static cudaError_t occupancy_t(int variant, bool opt, int* bps)
             return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[2], INTEG>, kRenderBlock, 0);
     }
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, render_kernel<R, kVariantBlocks[0], INTEG>, kRenderBlock, 0);
+    }
 }
 
 template <class R, int INTEG>
@@ -75,6 +80,9 @@ static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, flo
             sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br);
         return cudaGetLastError();
     }
+    if constexpr (INTEG == RT_RK4T) {
+        return cudaErrorInvalidValue;
+    } else {
     if constexpr (sizeof(R) == 4 && INTEG == RT_RK4) {
         if (variant == 1) {
             render_kernel<R, kVariantBlocks[1], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
@@ -87,6 +95,7 @@ static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, flo
     }
     render_kernel<R, kVariantBlocks[0], INTEG><<<grid, kRenderBlock, 0, stream>>>(sc, rgb, rgb8, rec, counters, min_active);
     return cudaGetLastError();
+    }
 }
 
 size_t branch_queue_bytes(int precision, int grid)
@@ -96,17 +105,22 @@ size_t branch_queue_bytes(int precision, int grid)
 
 bool variant_compiled(int precision, int integrator, int variant)
 {
-    if (variant == 0 || variant == kVariantWave) return true;
+    if (variant == kVariantWave) return true;
+    if (integrator == RT_RK4T) return false;
+    if (variant == 0) return true;
     return precision == RT_FP32 && integrator == RT_RK4 && variant >= 0 && variant < kLaneVariants;
 }
 
 cudaError_t render_occupancy(int precision, int integrator, int variant, bool opt, int* blocks_per_sm)
 {
-    if (precision == RT_FP64)
-        return integrator == RT_DP45 ? occupancy_t<double, RT_DP45>(variant, opt, blocks_per_sm)
-                                     : occupancy_t<double, RT_RK4>(variant, opt, blocks_per_sm);
-    return integrator == RT_DP45 ? occupancy_t<float, RT_DP45>(variant, opt, blocks_per_sm)
-                                 : occupancy_t<float, RT_RK4>(variant, opt, blocks_per_sm);
+    if (precision == RT_FP64) {
+        if (integrator == RT_DP45) return occupancy_t<double, RT_DP45>(variant, opt, blocks_per_sm);
+        if (integrator == RT_RK4T) return occupancy_t<double, RT_RK4T>(variant, opt, blocks_per_sm);
+        return occupancy_t<double, RT_RK4>(variant, opt, blocks_per_sm);
+    }
+    if (integrator == RT_DP45) return occupancy_t<float, RT_DP45>(variant, opt, blocks_per_sm);
+    if (integrator == RT_RK4T) return occupancy_t<float, RT_RK4T>(variant, opt, blocks_per_sm);
+    return occupancy_t<float, RT_RK4>(variant, opt, blocks_per_sm);
 }
 
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
@@ -116,10 +130,14 @@ cudaError_t launch_render(const DevScene& sc, int precision, int variant, int mi
     if (precision == RT_FP64) {
         if (sc.integrator == RT_DP45)
             return launch_t<double, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
+        if (sc.integrator == RT_RK4T)
+            return launch_t<double, RT_RK4T>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
         return launch_t<double, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
     }
     if (sc.integrator == RT_DP45)
         return launch_t<float, RT_DP45>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
+    if (sc.integrator == RT_RK4T)
+        return launch_t<float, RT_RK4T>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
     return launch_t<float, RT_RK4>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream);
 }
 

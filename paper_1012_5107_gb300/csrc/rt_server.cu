@@ -226,7 +226,7 @@ static void worker_main(rt_server* S)
             int kind = -1;
             while (!S->queue.empty() && admit.size() < 256) {
                 Request& r = S->req[S->queue.front()];
-                const int k = r.desc.precision * 2 + r.desc.integrator;
+                const int k = r.desc.precision * 4 + r.desc.integrator;
                 if (kind >= 0 && k != kind) break;
                 if (S->in_use + r.bytes > S->budget) break;
                 kind = k;

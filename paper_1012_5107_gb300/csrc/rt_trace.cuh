@@ -284,6 +284,79 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
 }
 
+// ------------------------------------------------------------------------
+// RK4 on Eq. 11 in physical time t (RT_RK4T).
+// ------------------------------------------------------------------------
+// The box state carries the velocity v (|v| = c0/n, c0 = 1) in px, py, pz.
+// With F = n grad n, the force of the tau form (scaled by s^2 like it), the
+// acceleration of Eq. 11 is dv/dt = (|v|^2 grad n - 2 (grad n . v) v) / n
+// = (|v|^2 F - 2 (F . v) v) / n^2, n^2 = s^2 |r|^2; F has no z component.
+template <class R>
+__device__ __forceinline__ void accel_t(const StepConst<R>& k, R Fx, R Fy, R vx, R vy, R vz, R rr, R ri, R& ax,
+                                        R& ay, R& az)
+{
+    const R in2 = k.is2 * Mth<R>::rcp(rr * rr + ri * ri);
+    const R v2 = vx * vx + vy * vy + vz * vz;
+    const R g2 = R(2) * (Fx * vx + Fy * vy);
+    ax = (v2 * Fx - g2 * vx) * in2;
+    ay = (v2 * Fy - g2 * vy) * in2;
+    az = -(g2 * vz) * in2;
+}
+
+// One classical RK4 step of size h (in t) on the first-order system
+// (r, v)' = (v, a(r, v)) from s (W0 solved and F known at s) into o; o's W0
+// is continued to the end point but not solved.  v_z changes along the ray
+// (n^2 v_z is the conserved momentum) and is summed without compensation.
+template <class R>
+__device__ __forceinline__ void rk4t_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
+{
+    const R h2 = R(0.5) * h;
+    R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
+    R a1x, a1y, a1z;
+    accel_t(k, s.Fx, s.Fy, s.px, s.py, s.pz, rr, ri, a1x, a1y, a1z);
+    R Fx, Fy;
+    // stage 2 at (r + h/2 v, v + h/2 a1)
+    const R v2x = s.px + h2 * a1x, v2y = s.py + h2 * a1y, v2z = s.pz + h2 * a1z;
+    const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
+    w0_continue(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
+    ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    R a2x, a2y, a2z;
+    accel_t(k, Fx, Fy, v2x, v2y, v2z, rr, ri, a2x, a2y, a2z);
+    // stage 3 at (r + h/2 v2, v + h/2 a2)
+    const R v3x = s.px + h2 * a2x, v3y = s.py + h2 * a2y, v3z = s.pz + h2 * a2z;
+    const R X3 = s.X + h2 * v2x, y3 = s.y + h2 * v2y;
+    w0_continue(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
+    ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    R a3x, a3y, a3z;
+    accel_t(k, Fx, Fy, v3x, v3y, v3z, rr, ri, a3x, a3y, a3z);
+    // stage 4 at (r + h v3, v + h a3)
+    const R v4x = s.px + h * a3x, v4y = s.py + h * a3y, v4z = s.pz + h * a3z;
+    const R X4 = s.X + h * v3x, y4 = s.y + h * v3y;
+    w0_continue(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
+    ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    R a4x, a4y, a4z;
+    accel_t(k, Fx, Fy, v4x, v4y, v4z, rr, ri, a4x, a4y, a4z);
+    // increments h/6 (k1 + 2 k2 + 2 k3 + k4) of both halves of the state
+    const R h6 = h * R(1.0 / 6.0);
+    const R dX = h6 * (s.px + R(2) * (v2x + v3x) + v4x);
+    const R dY = h6 * (s.py + R(2) * (v2y + v3y) + v4y);
+    const R dZ = h6 * (s.pz + R(2) * (v2z + v3z) + v4z);
+    const R dVx = h6 * (a1x + R(2) * (a2x + a3x) + a4x);
+    const R dVy = h6 * (a1y + R(2) * (a2y + a3y) + a4y);
+    const R dVz = h6 * (a1z + R(2) * (a2z + a3z) + a4z);
+    o = s;
+    kahan_add(o.X, o.cX, dX);
+    kahan_add(o.y, o.cy, dY);
+    kahan_add(o.z, o.cz, dZ);
+    kahan_add(o.px, o.cpx, dVx);
+    kahan_add(o.py, o.cpy, dVy);
+    o.pz += dVz;
+    w0_predict(wr, wi, rr, ri, o.X - X4, o.y - y4);
+    o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
+    if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
+    else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+}
+
 // Dormand & Prince (1980) RK5(4)7M: nodes, coefficients, fifth-order weights
 // and the differences between the fifth- and fourth-order weights.
 struct DPT {
@@ -446,6 +519,8 @@ __device__ __forceinline__ void integ_step(const StepConst<R>& k, const Box<R>& 
     if constexpr (INTEG == RT_DP45) {
         R e[4];
         dp45_step(k, s, h, o, e, st);
+    } else if constexpr (INTEG == RT_RK4T) {
+        rk4t_step(k, s, h, o, st);
     } else {
         rk4_step(k, s, h, o, st);
     }
@@ -918,7 +993,7 @@ __device__ bool plate_traverse(const DevScene& sc, Cold<R>& C, double P[3], doub
     }
 }
 
-template <class R, bool OPT>
+template <class R, int INTEG, bool OPT>
 __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
                             rt_ray_record* rec, LaneStats& st)
 {
@@ -986,9 +1061,11 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL)
                 fresnel_split(C, fresnel_R(1.0, sqrt(n2), pn, pin), MED_AIR, C.cx, C.X, C.y, C.z,
                               d[0] - 2.0 * pn * N[0], d[1] - 2.0 * pn * N[1], d[2] - 2.0 * pn * N[2], EV_NONE, steps);
-            b.px = (R)(pt[0] - pin * N[0]);
-            b.py = (R)(pt[1] - pin * N[1]);
-            b.pz = (R)(pt[2] - pin * N[2]);
+            // the momentum |p| = n inside; the time form carries v = p / n^2
+            const double iv = (INTEG == RT_RK4T) ? 1.0 / n2 : 1.0;
+            b.px = (R)((pt[0] - pin * N[0]) * iv);
+            b.py = (R)((pt[1] - pin * N[1]) * iv);
+            b.pz = (R)((pt[2] - pin * N[2]) * iv);
             b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
             b.hc = k.h;
             ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
@@ -1087,18 +1164,23 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     }
     // a face: refract into air (n = 1) or reflect totally; Snell's law in
     // FP64 since sqrt(1 - |p_t|^2) is ill-conditioned near grazing exit
+    // (the time form converts its velocity to the momentum p = n^2 v first)
     R Nf[3];
     face_normal(ev_best, Nf);
-    const double p[3] = {(double)b.px, (double)b.py, (double)b.pz};
+    double n2f = 1.0;
+    if constexpr (INTEG == RT_RK4T)
+        n2f = ((double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri) / (double)k.is2;
+    const double p[3] = {(double)b.px * n2f, (double)b.py * n2f, (double)b.pz * n2f};
     const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
     const double pn = p[0] * N[0] + p[1] * N[1] + p[2] * N[2];
     double pt[3];
     for (int a = 0; a < 3; ++a) pt[a] = p[a] - pn * N[a];
     const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
     if (pt2 >= 1.0) {
-        b.px = (R)(p[0] - 2.0 * pn * N[0]);
-        b.py = (R)(p[1] - 2.0 * pn * N[1]);
-        b.pz = (R)(p[2] - 2.0 * pn * N[2]);
+        const double vn = pn / n2f;
+        b.px = (R)((double)b.px - 2.0 * vn * N[0]);
+        b.py = (R)((double)b.py - 2.0 * vn * N[1]);
+        b.pz = (R)((double)b.pz - 2.0 * vn * N[2]);
         b.cpx = b.cpy = R(0);
         C.bounces++;
         surf = ev_best;
@@ -1189,7 +1271,8 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         o.hc = fmin(hs * fac, k.hmax);
     } else {
         hs = k.h;
-        rk4_step(k, s, hs, o, st);
+        if constexpr (INTEG == RT_RK4T) rk4t_step(k, s, hs, o, st);
+        else rk4_step(k, s, hs, o, st);
         w0_eval(k, o.X, o.y, o.wr, o.wi, o.rr, o.ri, st);
         ray_force(o.wr, o.wi, o.rr, o.ri, k.fk, o.Fx, o.Fy);
         ++steps;
@@ -1260,7 +1343,7 @@ __device__ __forceinline__ void start_sample(const DevScene& sc, Cold<R>& C, int
 
 // Start the next queued Fresnel branch of the sample in place of the path
 // that just ended (phase becomes PH_AIR or PH_BOX).
-template <class R>
+template <class R, int INTEG>
 __device__ void start_branch(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int& steps,
                              LaneStats& st)
 {
@@ -1285,6 +1368,13 @@ __device__ void start_branch(const DevScene& sc, Cold<R>& C, Box<R>& b, int& pha
         b.wr = b.wi = R(0);
         w0_eval(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
         ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
+        if constexpr (INTEG == RT_RK4T) {
+            // the branch holds the momentum; the time form carries v = p / n^2
+            const double iv = (double)k.is2 / ((double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri);
+            b.px = (R)((double)q.p[0] * iv);
+            b.py = (R)((double)q.p[1] * iv);
+            b.pz = (R)((double)q.p[2] * iv);
+        }
         b.hc = k.h;
         phase = PH_BOX;
     } else {
@@ -1438,7 +1528,7 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
                 start_sample<R, false>(src.scene(s), C, phase, surf, steps);
             }
             const DevScene& sc = src.scene(C.scene);
-            if (phase == PH_AIR) air_segment<R, false>(sc, C, b, phase, surf, steps, src.rec_of(C.scene), st);
+            if (phase == PH_AIR) air_segment<R, INTEG, false>(sc, C, b, phase, surf, steps, src.rec_of(C.scene), st);
             if (phase == PH_DONE) {
                 if (++C.sample < sc.spp) {
                     start_sample<R, false>(sc, C, phase, surf, steps);

@@ -329,10 +329,10 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                         start_sample<R, OPT>(src.scene(s), C, phase, surf, steps);
                     }
                     const DevScene& scs = src.scene(C.scene);
-                    if (phase == PH_AIR) air_segment<R, OPT>(scs, C, b, phase, surf, steps, src.rec_of(C.scene), st);
+                    if (phase == PH_AIR) air_segment<R, INTEG, OPT>(scs, C, b, phase, surf, steps, src.rec_of(C.scene), st);
                     if (phase == PH_DONE) {
                         if (OPT && C.ibr < C.nbr) {
-                            start_branch(scs, C, b, phase, surf, steps, st);   // next Fresnel branch
+                            start_branch<R, INTEG>(scs, C, b, phase, surf, steps, st);   // next Fresnel branch
                         } else {
                             rt_ray_record* rec = src.rec_of(C.scene);
                             if (rec && (opt_flags<OPT>(scs) & RT_FLAG_FRESNEL)) {

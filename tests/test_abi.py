@@ -48,6 +48,7 @@ def test_version(rt):
 @pytest.mark.parametrize("bad,field", [
     (dict(Lambda=0.0), "Lambda"), (dict(A=0.2), "A must"), (dict(width=0), "width"),
     (dict(hfov_deg=180.0), "hfov"), (dict(H=0.05), "H > 2A"), (dict(integrator=7), "integrator"),
+    (dict(integrator=3), "integrator"),
     (dict(precision=3), "precision"), (dict(background=1, tex_size=0), "texture"),
     (dict(mirror=0, cloak=1), "trochoid"), (dict(flags=8), "unknown bits"), (dict(max_steps=0), "max_steps"),
     (dict(flags=2), "plate lies on the flat mirror"),
@@ -84,6 +85,7 @@ def test_struct_layouts_match_header(rt, tmp_path):
 
 def test_validate_desc_on_host(rt):
     rt.validate(inputs.base_scene())
+    rt.validate(inputs.base_scene(integrator=2))          # RK4 in physical time (Eq. 11)
     with pytest.raises(rt.RtError) as e:
         rt.validate(inputs.base_scene(spp=0))
     assert e.value.code == rt.RT_EINVAL

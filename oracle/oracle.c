@@ -33,6 +33,11 @@
  *   - the referenced cloak (Figs. 5-7) divides the index inside the box by
  *     n_min = 1/(1 + kA); its ideal reference is a homogeneous plate of index
  *     1 + kA filling the box from the flat mirror (y = 0) to the box top;
+ *   - the Gaussian conformal cloak (Fig. 1(b), Fig. 4) is the map
+ *     z(w) = w + i h F(w/w_b) with F the Faddeeva function: it bounds the
+ *     bump by the image of v = 0, which tends to Eq. 5 for shallow bumps, and
+ *     at w_b = 0.306, h = 0.13 it gives the printed n_min = 0.873 and
+ *     n/n_min in [1, 2.2]; its box spans y = 0 (the flat mirror) to H;
  *   - the photograph (Fig. 2a) is replaced by a synthetic background plane.
  *
  * Parity unpinned: 3-D rays (p_z != 0) and total internal reflection at the
@@ -61,11 +66,14 @@ typedef struct or_scene {
     double bg_cell, tex_texel;
     double colour0[3], colour1[3];    /* checkerboard colours in [0,1]                       */
     double h, rtol, atol, h_max;      /* integrator parameters (world units)                 */
+    double gauss_w;                   /* Gaussian bump width w (mirror 2); its height is A    */
     uint64_t seed, scene_id;
     int64_t max_steps;
     const float* tex;                 /* tex_size x tex_size greyscale, row-major            */
-    int32_t mirror;                   /* 0 flat plane y=0, 1 trochoid grating (Eq. 2)        */
-    int32_t cloak;                    /* 1: graded-index box of Eq. 1 above the grating      */
+    int32_t mirror;                   /* 0 flat plane y=0, 1 trochoid grating (Eq. 2),
+                                         2 Gaussian bump (Eq. 5, exact form below)           */
+    int32_t cloak;                    /* 1: graded-index box above the mirror: Eq. 1 for the
+                                         grating, the Gaussian conformal map for the bump    */
     int32_t width, height, spp, centre_line;
     int32_t background;               /* 0 checkerboard, 1 texture                           */
     int32_t tex_size, integrator;     /* integrator: 0 RK4 fixed step, 1 Dormand-Prince 5(4) */
@@ -148,18 +156,135 @@ static double complex or_zeta(const or_scene* sc, double x, double y)
     return I * c * k * cexp(I * k * (x + I * y));
 }
 
-/* Index n (Eq. 1) and its gradient (Eq. 12) at (x, y); W0 is returned too. */
-static void or_medium(const or_scene* sc, double x, double y, double complex* W,
+/* ------------------------------------------------------------------------ */
+/* Faddeeva function F(s) = exp(-s^2) erfc(-i s), for the Gaussian cloak.    */
+/* Weideman (1994), "Computation of the complex error function", SIAM J.    */
+/* Numer. Anal. 31, 1497-1518: for Im s >= 0                                 */
+/*   F(s) ~ 1/(sqrt(pi) (L - i s)) + 2/(L - i s)^2 sum_{n<N} a_{n+1} Z^n,    */
+/*   Z = (L + i s)/(L - i s),  L = 2^(-1/4) N^(1/2),                         */
+/* with a_n the Fourier coefficients (in theta) of (L^2 + t^2) exp(-t^2),    */
+/* t = L tan(theta/2); here N = 48 and the coefficients come from the        */
+/* midpoint rule on 8192 angles.  Below the real axis the reflection         */
+/* F(s) = 2 exp(-s^2) - F(-s) holds.                                         */
+/* ------------------------------------------------------------------------ */
+#define OR_WN 48
+static double or_wa[OR_WN];
+static double or_wL;
+static int or_wready;
+
+/* Fills the coefficient table; called once when the library is loaded,
+   before any evaluation. */
+void or_init(void)
+{
+    if (or_wready) return;
+    const int M = 8192;
+    const double L = pow(2.0, -0.25) * sqrt((double)OR_WN);
+    for (int n = 1; n <= OR_WN; ++n) {
+        double acc = 0.0;
+        for (int j = 0; j < M; ++j) {
+            const double th = -OR_PI + (j + 0.5) * (2.0 * OR_PI / M);
+            const double t = L * tan(0.5 * th);
+            acc += (L * L + t * t) * exp(-t * t) * cos(n * th);
+        }
+        or_wa[n - 1] = acc / M;
+    }
+    or_wL = L;
+    or_wready = 1;
+}
+
+static double complex or_faddeeva_upper(double complex s)
+{
+    const double complex d = or_wL - I * s;
+    const double complex Z = (or_wL + I * s) / d;
+    double complex p = 0.0;
+    for (int n = OR_WN - 1; n >= 0; --n) p = p * Z + or_wa[n];
+    return 2.0 * p / (d * d) + 1.0 / (sqrt(OR_PI) * d);
+}
+
+static double complex or_faddeeva(double complex s)
+{
+    if (!or_wready) return NAN;                    /* or_init was not called */
+    if (cimag(s) >= 0.0) return or_faddeeva_upper(s);
+    return 2.0 * cexp(-s * s) - or_faddeeva_upper(-s);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Gaussian conformal map (Sec. 2, Fig. 1(b), Fig. 4).  Reading: the virtual  */
+/* half plane v >= 0 (flat mirror at v = 0) maps onto the region above the   */
+/* bump by                                                                   */
+/*     z(w) = w + i h F(w / w_b),                                            */
+/* the analytic function of the upper half plane whose boundary image is    */
+/*     x = u - h Im F(u/w_b),  y = h Re F(u/w_b) = h exp(-(u/w_b)^2):        */
+/* in the shallow-bump limit this is Eq. 5, and the exact bump is implicit  */
+/* in x.  n = |dw/dz| = 1/|z'(w)|.  (h = A, w_b = gauss_w.)                  */
+/* ------------------------------------------------------------------------ */
+static void or_gauss_z(const or_scene* sc, double complex w, double complex* z, double complex* dz,
+                       double complex* d2z)
+{
+    const double hb = sc->A, wb = sc->gauss_w;
+    const double complex s = w / wb;
+    const double complex F = or_faddeeva(s);
+    const double complex F1 = -2.0 * s * F + 2.0 * I / sqrt(OR_PI);   /* F'  */
+    const double complex F2 = -2.0 * F - 2.0 * s * F1;                 /* F'' */
+    if (z) *z = w + I * hb * F;
+    if (dz) *dz = 1.0 + I * hb * F1 / wb;
+    if (d2z) *d2z = I * hb * F2 / (wb * wb);
+}
+
+/* Virtual coordinate w of the physical point x + i y: Newton's method on
+   z(w) = x + i y from w = x + i y, each step limited to w_b / 4. */
+static double complex or_gauss_w(const or_scene* sc, double x, double y, int* iters)
+{
+    const double complex zt = x + I * y;
+    double complex w = zt;
+    *iters = 0;
+    for (int it = 1; it <= 100; ++it) {
+        double complex z, dz;
+        or_gauss_z(sc, w, &z, &dz, NULL);
+        double complex dw = (z - zt) / dz;
+        const double m = cabs(dw), cap = 0.25 * sc->gauss_w;
+        if (m > cap) dw *= cap / m;
+        w -= dw;
+        *iters = it;
+        if (!(m > 4.0 * DBL_EPSILON * (1.0 + cabs(w)))) break;
+    }
+    return w;
+}
+
+/* Index n and grad n at (x, y), with the virtual coordinate w (v = Im w is
+   the mirror's event function) and g = dw/dz (grad v = (Im g, Re g)).
+   Grating: Eq. 1 and Eq. 12, with w = z + i W0/k and g = 1/(1 + W0).
+   Gaussian cloak: n = |g|, and with g' = d^2w/dz^2 = -z''(w) g^3,
+   grad(n^2)/2 = (Re(conj(g) g'), -Im(conj(g) g')). */
+static void or_medium(const or_scene* sc, double x, double y, double complex* wv, double complex* gw,
                       double* n, double gn[3], counters* cnt)
 {
     int it;
+    if (sc->mirror == 2) {
+        const double complex w = or_gauss_w(sc, x, y, &it);
+        if (cnt) { cnt->halley += it; cnt->evals += 1; }
+        double complex dz, d2z;
+        or_gauss_z(sc, w, NULL, &dz, &d2z);
+        const double complex g = 1.0 / dz;
+        const double complex g1 = -d2z * g * g * g;
+        const double complex q = conj(g) * g1;
+        *n = cabs(g);
+        gn[0] = creal(q) / *n;
+        gn[1] = -cimag(q) / *n;
+        gn[2] = 0.0;
+        if (wv) *wv = w;
+        if (gw) *gw = g;
+        return;
+    }
     const double k = 2.0 * OR_PI / sc->Lambda;
-    *W = or_w0_c(or_zeta(sc, x, y), &it);
+    const double complex Wl = or_w0_c(or_zeta(sc, x, y), &it);
+    if (wv) *wv = (x + I * y) + I * Wl / k;
+    if (gw) *gw = 1.0 / (1.0 + Wl);
     if (cnt) { cnt->halley += it; cnt->evals += 1; }
-    const double complex onepw = 1.0 + *W;
+    const double complex onepw = 1.0 + Wl;
     const double m = cabs(onepw);                 /* |1 + W0| */
     const double re1 = creal(onepw);               /* Re(1 + W0) */
-    const double imw = cimag(*W);                  /* Im(W0)     */
+    const double imw = cimag(Wl);                  /* Im(W0)     */
     *n = 1.0 / m;
     gn[0] = (2.0 * re1 * imw / (m * m) - imw) * k / (m * m * m);
     gn[1] = ((imw * imw - re1 * re1) / (m * m) + re1) * k / (m * m * m);
@@ -194,9 +319,8 @@ static double or_fresnel_R(double n1, double n2, double pn1, double pn2)
    the integrator is only run inside the box, so the force is always Eq. 12's. */
 static void or_rhs(const or_scene* sc, const double s[6], double ds[6], counters* cnt)
 {
-    double complex W;
     double n, gn[3];
-    or_medium(sc, s[0], s[1], &W, &n, gn, cnt);
+    or_medium(sc, s[0], s[1], NULL, NULL, &n, gn, cnt);
     ds[0] = s[3]; ds[1] = s[4]; ds[2] = s[5];
     if (sc->integrator == 2) {
         /* Eq. 11 in physical time t (c0 = 1): the state is (r, v), |v| = 1/n,
@@ -322,6 +446,66 @@ static double or_trochoid_slope(const or_scene* sc, double x)
 }
 
 /* ------------------------------------------------------------------------ */
+/* Gaussian bump, the image of v = 0 under the Gaussian conformal map:      */
+/* x = u - h Im F(u/w_b), y = h exp(-(u/w_b)^2) (Eq. 5 in the shallow limit). */
+/* ------------------------------------------------------------------------ */
+
+/* Bump parameter u at abscissa x; x(u) is increasing for h/w_b < sqrt(pi)/2
+   and |x - u| <= 0.62 h, so Newton's method is guarded by bisection on
+   [x - h, x + h]. */
+static double or_bump_u(const or_scene* sc, double x)
+{
+    const double hb = sc->A, wb = sc->gauss_w;
+    double lo = x - hb, hi = x + hb, u = x;
+    for (int it = 0; it < 200; ++it) {
+        const double complex F = or_faddeeva(u / wb);
+        const double f = u - hb * cimag(F) - x;
+        if (f > 0) hi = u; else lo = u;
+        const double dxdu = 1.0 - (hb / wb) * cimag(-2.0 * (u / wb) * F + 2.0 * I / sqrt(OR_PI));
+        double un = u - f / dxdu;
+        if (!(un > lo && un < hi)) un = 0.5 * (lo + hi);
+        const double d = fabs(un - u);
+        u = un;
+        if (d <= 4.0 * DBL_EPSILON * fmax(1.0, fabs(u))) break;
+    }
+    return u;
+}
+
+/* Tangent (dx/du, dy/du) = z'(u) of the bump at parameter u. */
+static void or_bump_tangent(const or_scene* sc, double u, double T[2])
+{
+    double complex dz;
+    or_gauss_z(sc, u, NULL, &dz, NULL);
+    T[0] = creal(dz); T[1] = cimag(dz);
+}
+
+/* Mirror surface of kind 1 (trochoid) or 2 (bump): height, slope and
+   upward unit normal at abscissa x. */
+static double or_surface_y(const or_scene* sc, double x)
+{
+    if (sc->mirror != 2) return or_trochoid_y(sc, x);
+    const double u = or_bump_u(sc, x) / sc->gauss_w;
+    return sc->A * exp(-u * u);
+}
+
+static double or_surface_slope(const or_scene* sc, double x)
+{
+    if (sc->mirror != 2) return or_trochoid_slope(sc, x);
+    double T[2];
+    or_bump_tangent(sc, or_bump_u(sc, x), T);
+    return T[1] / T[0];
+}
+
+static void or_surface_normal(const or_scene* sc, double x, double N[3])
+{
+    if (sc->mirror != 2) { or_trochoid_normal(sc, x, N); return; }
+    double T[2];
+    or_bump_tangent(sc, or_bump_u(sc, x), T);
+    const double l = sqrt(T[0] * T[0] + T[1] * T[1]);
+    N[0] = -T[1] / l; N[1] = T[0] / l; N[2] = 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
 /* Illinois (modified regula falsi) root finder on a bracket [a, b] with     */
 /* fa > 0 >= fb.  The function is given by a callback.                       */
 /* ------------------------------------------------------------------------ */
@@ -364,36 +548,38 @@ typedef struct line_ctx {
 static double or_line_height(void* vctx, double t)
 {
     line_ctx* c = (line_ctx*)vctx;
-    double h = (c->X[1] + t * c->p[1]) - or_trochoid_y(c->sc, c->X[0] + t * c->p[0]);
+    double h = (c->X[1] + t * c->p[1]) - or_surface_y(c->sc, c->X[0] + t * c->p[0]);
     return c->deflate ? h / t : h;
 }
 
-/* First t > 0 at which the line X + t p meets the trochoid (Eq. 2), or
-   INFINITY.  The line is marched in increments that move the point by at most
-   Lambda/(8 pi) in the xy-plane; the first increment at whose end the line is
-   at or below the surface brackets the hit, which is then refined.  When the
-   line starts on the surface (just reflected there), the zero at t = 0 is
-   divided out. */
+/* First t > 0 at which the line X + t p meets the trochoid (Eq. 2) or the
+   Gaussian bump, or INFINITY.  Inside the band the surface spans (y in
+   [-A, A], resp. [0, h]) the line is marched in increments that move the
+   point by at most Lambda/(8 pi) (resp. w_b/8) in the xy-plane; the first
+   increment at whose end the line is at or below the surface brackets the
+   hit, which is then refined.  When the line starts on the surface (just
+   reflected there), the zero at t = 0 is divided out. */
 static double or_trochoid_line_hit(const or_scene* sc, const double X[3], const double p[3],
                                    int on_surface)
 {
-    const double A = sc->A, k = 2.0 * OR_PI / sc->Lambda;
+    const int bump = sc->mirror == 2;
+    const double ylo = bump ? 0.0 : -sc->A, yhi = sc->A;
     const double dxy = sqrt(p[0] * p[0] + p[1] * p[1]);
     if (dxy < 1e-300) return INFINITY;
-    if (p[1] >= 0.0 && X[1] >= A) return INFINITY;
+    if (p[1] >= 0.0 && X[1] >= yhi) return INFINITY;
     double t0 = 0.0;
-    if (X[1] > A) t0 = (A - X[1]) / p[1];
+    if (X[1] > yhi) t0 = (yhi - X[1]) / p[1];
     double t_end;
-    if (p[1] < 0.0) t_end = (-A - X[1]) / p[1];
-    else if (p[1] > 0.0) t_end = (A - X[1]) / p[1];
-    else t_end = t0 + 2.0 * sc->Lambda / fabs(p[0]);
-    const double dt = 0.25 / (k * dxy);
+    if (p[1] < 0.0) t_end = (ylo - X[1]) / p[1];
+    else if (p[1] > 0.0) t_end = (yhi - X[1]) / p[1];
+    else t_end = t0 + 2.0 * (bump ? 20.0 * sc->gauss_w : sc->Lambda) / fabs(p[0]);
+    const double dt = bump ? 0.125 * sc->gauss_w / dxy : 0.25 / (2.0 * OR_PI / sc->Lambda * dxy);
     line_ctx ctx = {sc, {X[0], X[1], X[2]}, {p[0], p[1], p[2]}, 0};
     double ta = t0, ha;
     int first = on_surface && t0 == 0.0;
     if (first) {
         /* derivative of the height along the line at t = 0 */
-        ha = p[1] - or_trochoid_slope(sc, X[0]) * p[0];
+        ha = p[1] - or_surface_slope(sc, X[0]) * p[0];
         if (!(ha > 0.0)) ha = 1e-300;
     } else {
         ha = or_line_height(&ctx, ta);
@@ -407,7 +593,7 @@ static double or_trochoid_line_hit(const or_scene* sc, const double X[3], const 
             tb = fmin(1e-9 * sc->Lambda, t_end);
         }
         double hb = or_line_height(&ctx, tb);
-        /* a descending line meets the surface by y = -A at the latest */
+        /* a descending line meets the surface by the bottom of its band at the latest */
         if (tb >= t_end && p[1] < 0.0 && hb > 0.0) hb = 0.0;
         if (hb <= 0.0) {
             if (first) {
@@ -436,12 +622,24 @@ static double or_flat_line_hit(const double X[3], const double p[3])
 /* ------------------------------------------------------------------------ */
 /* Cloak box.                                                                */
 /* ------------------------------------------------------------------------ */
+/* The box spans |x|, |z| <= E/2 and, in y, H from the grating's troughs
+   (y = -A) or from the flat mirror under the bump (y = 0). */
+static double or_box_bottom(const or_scene* sc)
+{
+    if (sc->mirror == 2 || (sc->flags & OR_FLAG_PLATE)) return 0.0;   /* plate: on the flat mirror */
+    return -sc->A;
+}
+
+static double or_box_top(const or_scene* sc)
+{
+    return (sc->mirror == 2 ? 0.0 : -sc->A) + sc->H;
+}
+
 static void or_box(const or_scene* sc, double lo[3], double hi[3])
 {
     lo[0] = -0.5 * sc->E; hi[0] = 0.5 * sc->E;
-    lo[1] = -sc->A;       hi[1] = -sc->A + sc->H;
+    lo[1] = or_box_bottom(sc); hi[1] = or_box_top(sc);
     lo[2] = -0.5 * sc->E; hi[2] = 0.5 * sc->E;
-    if (sc->flags & OR_FLAG_PLATE) lo[1] = 0.0;   /* the plate lies on the flat mirror */
 }
 
 /* Entry of the line X + t p (t > 0) into the box by the slab method; returns
@@ -492,12 +690,12 @@ static double or_event_g(const or_scene* sc, int ev, const double s[6], counters
 {
     switch (ev) {
         case EV_GRATING: {
-            double complex W;
+            double complex wv;
             double n, gn[3];
-            or_medium(sc, s[0], s[1], &W, &n, gn, cnt);
-            return s[1] + creal(W) / (2.0 * OR_PI / sc->Lambda);   /* v = Im w = y + Re W0 / k */
+            or_medium(sc, s[0], s[1], &wv, NULL, &n, gn, cnt);
+            return cimag(wv);                      /* v = Im w (grating: y + Re W0 / k) */
         }
-        case EV_TOP: return (-sc->A + sc->H) - s[1];
+        case EV_TOP: return or_box_top(sc) - s[1];
         case EV_XP: return 0.5 * sc->E - s[0];
         case EV_XM: return 0.5 * sc->E + s[0];
         case EV_ZP: return 0.5 * sc->E - s[2];
@@ -510,12 +708,11 @@ static void or_event_grad(const or_scene* sc, int ev, const double s[6], double 
 {
     g[0] = g[1] = g[2] = 0.0;
     if (ev == EV_GRATING) {
-        /* grad v = (Im 1/(1+W), Re 1/(1+W)) since w = z + i W/k is analytic with w' = 1/(1+W) */
-        double complex W;
+        /* grad v = (Im g, Re g) since w is analytic with dw/dz = g (grating: g = 1/(1+W0)) */
+        double complex gw;
         double n, gn[3];
-        or_medium(sc, s[0], s[1], &W, &n, gn, cnt);
-        double complex r = 1.0 / (1.0 + W);
-        g[0] = cimag(r); g[1] = creal(r);
+        or_medium(sc, s[0], s[1], NULL, &gw, &n, gn, cnt);
+        g[0] = cimag(gw); g[1] = creal(gw);
         return;
     }
     double N[3];
@@ -763,9 +960,8 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
                 if (plate) {
                     n = or_plate_index(sc);
                 } else {
-                    double complex W;
                     double gn[3];
-                    or_medium(sc, X[0], X[1], &W, &n, gn, &cnt);
+                    or_medium(sc, X[0], X[1], NULL, NULL, &n, gn, &cnt);
                 }
                 const double pn = or_dot(p, Nf);
                 double pt[3];
@@ -793,7 +989,7 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
             if (t_m < INFINITY) {
                 for (int a = 0; a < 3; ++a) X[a] += t_m * p[a];
                 double N[3] = {0.0, 1.0, 0.0};
-                if (sc->mirror) or_trochoid_normal(sc, X[0], N);
+                if (sc->mirror) or_surface_normal(sc, X[0], N);
                 const double pn = or_dot(p, N);
                 for (int a = 0; a < 3; ++a) p[a] -= 2.0 * pn * N[a];
                 bounces++;
@@ -861,9 +1057,8 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
            the velocity v = p / n^2 (|v| = c0 / n with c0 = 1) instead. */
         double s[6] = {X[0], X[1], X[2], p[0], p[1], p[2]};
         if (sc->integrator == 2) {
-            double complex W;
             double n, gn[3];
-            or_medium(sc, X[0], X[1], &W, &n, gn, &cnt);
+            or_medium(sc, X[0], X[1], NULL, NULL, &n, gn, &cnt);
             for (int a = 0; a < 3; ++a) s[3 + a] = p[a] / (n * n);
         }
         double k1[6], k7[6];
@@ -940,7 +1135,7 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
             traj_push(tb, s);
             if (ev_best == EV_GRATING) {
                 double N[3];
-                or_trochoid_normal(sc, s[0], N);
+                or_surface_normal(sc, s[0], N);
                 const double pn = s[3] * N[0] + s[4] * N[1] + s[5] * N[2];
                 for (int a = 0; a < 3; ++a) s[3 + a] -= 2.0 * pn * N[a];
                 bounces++;
@@ -955,9 +1150,8 @@ static void or_trace_path(const or_scene* sc, const camera* cam, const double X0
             double pm[3] = {s[3], s[4], s[5]};
             double n2f = 1.0;
             if (sc->integrator == 2) {
-                double complex W;
                 double nf, gn[3];
-                or_medium(sc, s[0], s[1], &W, &nf, gn, &cnt);
+                or_medium(sc, s[0], s[1], NULL, NULL, &nf, gn, &cnt);
                 n2f = nf * nf;
                 for (int a = 0; a < 3; ++a) pm[a] *= n2f;
             }
@@ -1057,13 +1251,18 @@ int or_lambertw0(const double* z, int64_t count, double* w, int32_t* iters)
     return 0;
 }
 
-/* Per point: out[6*i..] = (Re W0, Im W0, n, dn/dx, dn/dy, dn/dz). */
+/* Per point: out[6*i..] = (Re W, Im W, n, dn/dx, dn/dy, dn/dz), W = W0 for
+   the grating and the virtual coordinate w for the Gaussian cloak. */
 int or_index(const or_scene* sc, const double* xy, int64_t count, double* out)
 {
     for (int64_t i = 0; i < count; ++i) {
         double complex W;
         double n, gn[3];
-        or_medium(sc, xy[2 * i], xy[2 * i + 1], &W, &n, gn, NULL);
+        or_medium(sc, xy[2 * i], xy[2 * i + 1], &W, NULL, &n, gn, NULL);
+        if (sc->mirror != 2) {
+            int it;
+            W = or_w0_c(or_zeta(sc, xy[2 * i], xy[2 * i + 1]), &it);
+        }
         out[6 * i + 0] = creal(W); out[6 * i + 1] = cimag(W); out[6 * i + 2] = n;
         out[6 * i + 3] = gn[0]; out[6 * i + 4] = gn[1]; out[6 * i + 5] = gn[2];
     }
@@ -1081,6 +1280,49 @@ int or_trochoid(const or_scene* sc, const double* x, int64_t count, double* out)
         out[4 * i + 2] = N[0]; out[4 * i + 3] = N[1];
     }
     return 0;
+}
+
+/* Faddeeva function at the points s (pairs Re, Im): out gets (Re F, Im F). */
+int or_faddeeva_eval(const double* s, int64_t count, double* out)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        const double complex F = or_faddeeva(s[2 * i] + I * s[2 * i + 1]);
+        out[2 * i] = creal(F);
+        out[2 * i + 1] = cimag(F);
+    }
+    return 0;
+}
+
+/* Gaussian conformal map at virtual points w (pairs): out gets
+   (Re z, Im z, Re z', Im z') per point. */
+int or_gauss_map(const or_scene* sc, const double* w, int64_t count, double* out)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        double complex z, dz;
+        or_gauss_z(sc, w[2 * i] + I * w[2 * i + 1], &z, &dz, NULL);
+        out[4 * i + 0] = creal(z); out[4 * i + 1] = cimag(z);
+        out[4 * i + 2] = creal(dz); out[4 * i + 3] = cimag(dz);
+    }
+    return 0;
+}
+
+/* Mirror surface (trochoid or bump) at abscissae x: (y_s, slope, N_x, N_y). */
+int or_surface(const or_scene* sc, const double* x, int64_t count, double* out)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        double N[3];
+        out[4 * i + 0] = or_surface_y(sc, x[i]);
+        out[4 * i + 1] = or_surface_slope(sc, x[i]);
+        or_surface_normal(sc, x[i], N);
+        out[4 * i + 2] = N[0]; out[4 * i + 3] = N[1];
+    }
+    return 0;
+}
+
+/* First hit of the line X + t p with the mirror surface (tests). */
+double or_surface_line_hit(const or_scene* sc, const double* X, const double* p, int32_t on_surface)
+{
+    return sc->mirror ? or_trochoid_line_hit(sc, X, p, on_surface) : or_flat_line_hit(X, p);
 }
 
 /* Fixed-step integration without events.  method 0: RK4, 1: fifth-order
@@ -1124,6 +1366,11 @@ static int or_scene_ok(const or_scene* sc)
 {
     if (sc->background == 1 && (!sc->tex || sc->tex_size <= 0)) return 0;
     if ((sc->flags & OR_FLAG_PLATE) && (sc->cloak || sc->mirror)) return 0;   /* the plate lies on the flat mirror */
+    if (sc->mirror < 0 || sc->mirror > 2) return 0;
+    if (sc->mirror == 2) {      /* the Gaussian map is one-to-one while h/w_b < sqrt(pi)/2 */
+        if (!(sc->gauss_w > 0.0) || !(sc->A >= 0.0) || !(sc->A < 0.8 * sc->gauss_w)) return 0;
+        if (sc->flags != 0) return 0;
+    }
     return 1;
 }
 

@@ -38,6 +38,7 @@ class OrScene(C.Structure):
         ("bg_cell", C.c_double), ("tex_texel", C.c_double),
         ("colour0", C.c_double * 3), ("colour1", C.c_double * 3),
         ("h", C.c_double), ("rtol", C.c_double), ("atol", C.c_double), ("h_max", C.c_double),
+        ("gauss_w", C.c_double),
         ("seed", C.c_uint64), ("scene_id", C.c_uint64),
         ("max_steps", C.c_int64),
         ("tex", C.POINTER(C.c_float)),
@@ -97,6 +98,12 @@ def lib():
         L.or_fresnel.restype = C.c_double
         L.or_trace_paths.argtypes = [C.POINTER(OrScene), dp, dp, C.c_int32, C.c_int32, C.c_void_p, dp, C.c_int32,
                                      C.POINTER(C.c_int32)]
+        L.or_faddeeva_eval.argtypes = [dp, C.c_int64, dp]
+        L.or_gauss_map.argtypes = [C.POINTER(OrScene), dp, C.c_int64, dp]
+        L.or_surface.argtypes = [C.POINTER(OrScene), dp, C.c_int64, dp]
+        L.or_surface_line_hit.argtypes = [C.POINTER(OrScene), dp, dp, C.c_int32]
+        L.or_surface_line_hit.restype = C.c_double
+        L.or_init()                   # coefficient table of the Faddeeva function
         _lib = L
     return _lib
 
@@ -146,7 +153,8 @@ def lambertw0(z) -> tuple[np.ndarray, np.ndarray]:
 
 
 def index(sc: Scene, x, y) -> np.ndarray:
-    """Rows (Re W0, Im W0, n, dn/dx, dn/dy, dn/dz) at the points (x, y)."""
+    """Rows (Re W, Im W, n, dn/dx, dn/dy, dn/dz) at the points (x, y): W = W0
+    for the grating cloak, the virtual coordinate w for the Gaussian cloak."""
     x, y = np.broadcast_arrays(np.asarray(x, float), np.asarray(y, float))
     xy = np.ascontiguousarray(np.stack([x.ravel(), y.ravel()], -1).reshape(-1))
     out = np.zeros((x.size, 6))
@@ -284,3 +292,37 @@ def max_threads() -> int:
 if __name__ == "__main__":  # pragma: no cover
     build(force="--force" in sys.argv)
     print(LIB)
+
+
+def faddeeva(s) -> np.ndarray:
+    """The oracle's Faddeeva function F(s) = exp(-s^2) erfc(-i s)."""
+    s = np.asarray(s, dtype=np.complex128)
+    ss = np.ascontiguousarray(np.stack([s.real.ravel(), s.imag.ravel()], -1).reshape(-1))
+    out = np.zeros_like(ss)
+    lib().or_faddeeva_eval(_dp(ss), s.size, _dp(out))
+    return (out[0::2] + 1j * out[1::2]).reshape(s.shape)
+
+
+def gauss_map(sc: Scene, w) -> tuple[np.ndarray, np.ndarray]:
+    """z(w) and z'(w) of the Gaussian conformal map at virtual points w."""
+    w = np.asarray(w, dtype=np.complex128)
+    ww = np.ascontiguousarray(np.stack([w.real.ravel(), w.imag.ravel()], -1).reshape(-1))
+    out = np.zeros(4 * w.size)
+    lib().or_gauss_map(sc.ref, _dp(ww), w.size, _dp(out))
+    out = out.reshape(-1, 4)
+    return (out[:, 0] + 1j * out[:, 1]).reshape(w.shape), (out[:, 2] + 1j * out[:, 3]).reshape(w.shape)
+
+
+def surface(sc: Scene, x) -> np.ndarray:
+    """Rows (y_s, dy_s/dx, N_x, N_y) of the mirror surface (trochoid or bump) at abscissae x."""
+    x = np.ascontiguousarray(np.atleast_1d(np.asarray(x, float)))
+    out = np.zeros((x.size, 4))
+    lib().or_surface(sc.ref, _dp(x), x.size, _dp(out))
+    return out
+
+
+def surface_line_hit(sc: Scene, X, p, on_surface: bool = False) -> float:
+    """First t > 0 at which X + t p meets the mirror surface (inf if none)."""
+    X = np.ascontiguousarray(np.asarray(X, float))
+    p = np.ascontiguousarray(np.asarray(p, float))
+    return float(lib().or_surface_line_hit(sc.ref, _dp(X), _dp(p), int(on_surface)))

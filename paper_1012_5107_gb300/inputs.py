@@ -16,7 +16,7 @@ import numpy as np
 
 RK4, DP45 = 0, 1
 FP32, FP64 = 0, 1
-FLAT, TROCHOID = 0, 1
+FLAT, TROCHOID, GAUSS = 0, 1, 2
 CHECKER, TEXTURE = 0, 1
 
 
@@ -70,7 +70,7 @@ def base_scene(**over) -> dict:
         Lambda=1.0, A=0.04, H=2.0, E=8.0,
         cam_dist=12.0, elev_deg=30.0, azim_deg=0.0, hfov_deg=50.0,
         bg_cell=0.5, tex_texel=1.0 / 32.0, colour0=c0, colour1=c1,
-        h=1.0 / 200.0, rtol=1e-7, atol=1e-7, h_max=1.0 / 16.0,
+        h=1.0 / 200.0, rtol=1e-7, atol=1e-7, h_max=1.0 / 16.0, gauss_w=0.306,
         seed=1, scene_id=0, max_steps=1 << 20,
         mirror=TROCHOID, cloak=1, width=64, height=64, spp=1, centre_line=0,
         background=CHECKER, tex_size=0, integrator=RK4, max_bounces=16,
@@ -86,7 +86,7 @@ def base_scene(**over) -> dict:
 def scale_scene(p: dict, lam: float) -> dict:
     """The same scene with every length multiplied by lam (renders are invariant)."""
     q = dict(p)
-    for key in ("Lambda", "A", "H", "E", "cam_dist", "bg_cell", "tex_texel", "h", "h_max", "atol"):
+    for key in ("Lambda", "A", "H", "E", "cam_dist", "bg_cell", "tex_texel", "h", "h_max", "atol", "gauss_w"):
         q[key] = p[key] * lam
     return q
 
@@ -98,6 +98,24 @@ def three_renders(p: dict) -> dict[str, dict]:
         "mirror": dict(p, mirror=FLAT, cloak=0),
         "bare": dict(p, mirror=TROCHOID, cloak=0),
         "cloak": dict(p, mirror=TROCHOID, cloak=1),
+    }
+
+
+def gauss_scene(**over) -> dict:
+    """The Gaussian conformal cloak of Fig. 1(b) and Fig. 4: bump width
+    w = 0.306 and height h = 0.13 (A holds h), cloak box 1.1 high above the
+    flat mirror and 8 wide, otherwise the base scene."""
+    q = dict(mirror=GAUSS, A=0.13, gauss_w=0.306, H=1.1)
+    q.update(over)
+    return base_scene(**q)
+
+
+def gauss_renders(p: dict) -> dict[str, dict]:
+    """Flat mirror, bare bump and cloaked bump versions of one scene (Fig. 4 a, b, c)."""
+    return {
+        "mirror": dict(p, mirror=FLAT, cloak=0),
+        "bare": dict(p, mirror=GAUSS, cloak=0),
+        "cloak": dict(p, mirror=GAUSS, cloak=1),
     }
 
 

@@ -57,6 +57,10 @@ extern "C" {
 /* scene kinds and options */
 #define RT_MIRROR_FLAT 0      /* plane y = 0 (Fig. 3a)                         */
 #define RT_MIRROR_TROCHOID 1  /* trochoid grating, Eq. 2 (Fig. 3b, 3c)         */
+#define RT_MIRROR_GAUSS 2     /* Gaussian bump (Fig. 4b, 4c): the image of the
+                                 flat mirror under z(w) = w + i A F(w/gauss_w),
+                                 F the Faddeeva function; Eq. 5 in its shallow
+                                 limit.  Height A, width gauss_w                */
 #define RT_BG_CHECKER 0       /* two-colour checkerboard                       */
 #define RT_BG_TEXTURE 1       /* greyscale texture, bilinear, wrapping         */
 #define RT_RK4 0              /* classical Runge-Kutta, fixed step h           */
@@ -109,7 +113,8 @@ extern "C" {
 typedef struct rt_scene_desc {
     double Lambda;            /* grating period (> 0)                           */
     double A;                 /* half peak-to-peak amplitude, 0 <= kA < 1       */
-    double H, E;              /* cloak box height above y=-A and x/z extent     */
+    double H, E;              /* cloak box height above y=-A (y=0 for the
+                                 Gaussian bump) and x/z extent                 */
     double cam_dist, elev_deg, azim_deg, hfov_deg;
     double bg_cell;           /* checkerboard cell size                         */
     double tex_texel;         /* texture texel size                             */
@@ -117,21 +122,26 @@ typedef struct rt_scene_desc {
     double h;                 /* RK4 step (in the ray parameter tau, |dr/dtau| = n); DP45 first step */
     double rtol, atol;        /* DP45 tolerances (atol in world length units)   */
     double h_max;             /* DP45 largest step                              */
+    double gauss_w;           /* Gaussian bump width (RT_MIRROR_GAUSS), > 0;
+                                 0 <= A < 0.8 gauss_w keeps the map one to one */
     uint64_t seed, scene_id;  /* jitter stream                                  */
     int64_t max_steps;        /* guard on integrator steps per ray              */
     const float* tex;         /* host, tex_size^2 row-major greyscale (TEXTURE) */
     int32_t mirror;           /* RT_MIRROR_*                                    */
-    int32_t cloak;            /* 1: graded-index cloak box present              */
+    int32_t cloak;            /* 1: graded-index cloak box present (Eq. 1 on the
+                                 trochoid, the Gaussian map on the bump)        */
     int32_t width, height;    /* image size                                     */
     int32_t spp;              /* samples per pixel                              */
     int32_t centre_line;      /* 1: render only the vertical centre line
                                  (height x 1 image, horizontal offset 0)        */
     int32_t background;       /* RT_BG_*                                        */
     int32_t tex_size;         /* texture side                                   */
-    int32_t integrator;       /* RT_RK4 | RT_DP45 | RT_RK4T                     */
+    int32_t integrator;       /* RT_RK4 | RT_DP45 | RT_RK4T (RK4T: not with the
+                                 Gaussian bump)                                 */
     int32_t precision;        /* RT_FP32 | RT_FP64                              */
     int32_t max_bounces;      /* guard on reflections per ray                   */
-    int32_t flags;            /* RT_FLAG_* (0: the plain method)                */
+    int32_t flags;            /* RT_FLAG_* (0: the plain method; 0 for the
+                                 Gaussian bump)                                 */
 } rt_scene_desc;
 
 /* Per-sample exit record: the start of the ray's final straight segment (its

@@ -84,13 +84,23 @@ static int validate(const rt_scene_desc* d)
 {
     RT_REQ(d, "desc is NULL");
     RT_REQ(d->Lambda > 0.0 && std::isfinite(d->Lambda), "Lambda must be finite and > 0");
-    const double kA = 2.0 * kPi * d->A / d->Lambda;
-    RT_REQ(d->A >= 0.0 && kA < 1.0, "A must satisfy 0 <= 2 pi A / Lambda < 1 (curtate trochoid)");
-    RT_REQ(d->mirror == RT_MIRROR_FLAT || d->mirror == RT_MIRROR_TROCHOID, "mirror must be RT_MIRROR_FLAT or RT_MIRROR_TROCHOID");
+    RT_REQ(d->mirror == RT_MIRROR_FLAT || d->mirror == RT_MIRROR_TROCHOID || d->mirror == RT_MIRROR_GAUSS,
+           "mirror must be RT_MIRROR_FLAT, RT_MIRROR_TROCHOID or RT_MIRROR_GAUSS");
     RT_REQ(d->cloak == 0 || d->cloak == 1, "cloak must be 0 or 1");
-    RT_REQ(!d->cloak || d->mirror == RT_MIRROR_TROCHOID, "the cloak needs the trochoid mirror");
-    RT_REQ(!d->cloak || (d->H > 2.0 * d->A && d->E > 0.0 && std::isfinite(d->H) && std::isfinite(d->E)),
-           "cloak box needs H > 2A and E > 0");
+    RT_REQ(!d->cloak || d->mirror != RT_MIRROR_FLAT, "the cloak needs the trochoid (or Gaussian) mirror");
+    if (d->mirror == RT_MIRROR_GAUSS) {
+        RT_REQ(d->gauss_w > 0.0 && std::isfinite(d->gauss_w), "gauss_w must be finite and > 0");
+        RT_REQ(d->A >= 0.0 && d->A < 0.8 * d->gauss_w, "the Gaussian bump needs 0 <= A < 0.8 gauss_w");
+        RT_REQ(!d->cloak || (d->H > d->A && d->E > 0.0 && std::isfinite(d->H) && std::isfinite(d->E)),
+               "cloak box needs H > A and E > 0 over the Gaussian bump");
+        RT_REQ(d->flags == 0, "flags: the Gaussian bump takes no options");
+        RT_REQ(d->integrator == RT_RK4 || d->integrator == RT_DP45, "the Gaussian bump needs RT_RK4 or RT_DP45");
+    } else {
+        const double kA = 2.0 * kPi * d->A / d->Lambda;
+        RT_REQ(d->A >= 0.0 && kA < 1.0, "A must satisfy 0 <= 2 pi A / Lambda < 1 (curtate trochoid)");
+        RT_REQ(!d->cloak || (d->H > 2.0 * d->A && d->E > 0.0 && std::isfinite(d->H) && std::isfinite(d->E)),
+               "cloak box needs H > 2A and E > 0");
+    }
     RT_REQ(d->width >= 1 && d->height >= 1 && d->spp >= 1, "width, height and spp must be >= 1");
     RT_REQ(d->centre_line == 0 || d->centre_line == 1, "centre_line must be 0 or 1");
     RT_REQ(d->hfov_deg > 0.0 && d->hfov_deg < 180.0, "hfov_deg must be in (0, 180)");
@@ -127,8 +137,11 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->kA = kTwoPi * s->A;
     s->H = d->H / L;
     s->E2 = 0.5 * d->E / L;
-    s->ytop = -s->A + s->H;
-    s->yrec = -s->A + s->H + 1.0;
+    // the box spans y = -A (the grating's troughs) or y = 0 (under the
+    // Gaussian bump) to H above that
+    const double ybox = d->mirror == RT_MIRROR_GAUSS ? 0.0 : -s->A;
+    s->ytop = ybox + s->H;
+    s->yrec = ybox + s->H + 1.0;
     const double te = d->elev_deg * kPi / 180.0, ph = d->azim_deg * kPi / 180.0, D = d->cam_dist / L;
     s->C[0] = -D * cos(te) * cos(ph);
     s->C[1] = D * sin(te);
@@ -187,8 +200,18 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->cf.fk = (float)s->cd.fk;
     s->cd.is2 = 1.0 / (s->idx_scale * s->idx_scale);
     s->cf.is2 = (float)s->cd.is2;
-    s->cd.ybot = (d->flags & RT_FLAG_PLATE) ? 0.0 : -s->A;
+    s->cd.ybot = ((d->flags & RT_FLAG_PLATE) || d->mirror == RT_MIRROR_GAUSS) ? 0.0 : -s->A;
     s->cf.ybot = (float)s->cd.ybot;
+    // Gaussian bump: width, 1/width, k h, h/width, the Newton stop on W and
+    // the largest Newton step (a quarter width in w)
+    if (d->mirror == RT_MIRROR_GAUSS) {
+        const double gw = d->gauss_w / L;
+        s->cd.gw = gw; s->cd.igw = 1.0 / gw; s->cd.gkh = kTwoPi * s->A; s->cd.gq = s->A / gw;
+        s->cd.gtol = 1.6e-29;
+        s->cd.gcap2 = (0.25 * kTwoPi * gw) * (0.25 * kTwoPi * gw);
+        s->cf.gw = (float)gw; s->cf.igw = (float)(1.0 / gw); s->cf.gkh = (float)s->cd.gkh;
+        s->cf.gq = (float)s->cd.gq; s->cf.gtol = 1e-12f; s->cf.gcap2 = (float)s->cd.gcap2;
+    }
     for (int a = 0; a < 3; ++a) {
         s->ad.fr[a] = s->fr[a]; s->ad.ur[a] = s->ur[a]; s->ad.r[a] = s->r[a]; s->ad.Pb[a] = s->Pb[a];
         s->af.fr[a] = (float)s->fr[a]; s->af.ur[a] = (float)s->ur[a]; s->af.r[a] = (float)s->r[a];
@@ -198,8 +221,8 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->ad.inv_texel = s->texel > 0.0 ? 1.0 / s->texel : 0.0;
     s->af.inv_cell = (float)s->ad.inv_cell;
     s->af.inv_texel = (float)s->ad.inv_texel;
-    s->ymirror = d->mirror == RT_MIRROR_TROCHOID ? s->A : 0.0;
-    s->box_lo[0] = -s->E2; s->box_lo[1] = (d->flags & RT_FLAG_PLATE) ? 0.0 : -s->A; s->box_lo[2] = -s->E2;
+    s->ymirror = d->mirror != RT_MIRROR_FLAT ? s->A : 0.0;
+    s->box_lo[0] = -s->E2; s->box_lo[1] = s->cd.ybot; s->box_lo[2] = -s->E2;
     s->box_hi[0] = s->E2; s->box_hi[1] = s->ytop; s->box_hi[2] = s->E2;
     s->inv_m = s->m > 0 ? 1.0 / s->m : 0.0;
     s->two_over_w = 2.0 / (double)d->width;
@@ -266,7 +289,8 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     int bps = 0;
     s->variant = kDefaultVariant;
     s->min_active = kMinActive;
-    cudaError_t e = render_occupancy(desc->precision, desc->integrator, s->variant, desc->flags != 0, &bps);
+    cudaError_t e = desc->mirror == RT_MIRROR_GAUSS ? gauss_upload() : cudaSuccess;
+    if (e == cudaSuccess) e = render_occupancy(desc->precision, render_mode(*desc), s->variant, desc->flags != 0, &bps);
     int nsm = 0;
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     s->nsm = nsm;
@@ -432,7 +456,7 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
         float best = 1e30f;
         int rc = RT_OK;
         for (int var = 0; var < kVariants && rc == RT_OK; ++var) {
-            if (!variant_compiled(d.precision, d.integrator, var)) continue;
+            if (!variant_compiled(d.precision, render_mode(d), var)) continue;
             if (d.flags != 0 && var != kVariantWave) continue;
             for (int c : cand) {
                 rc = rt_scene_set_launch(s, var, c);
@@ -468,14 +492,14 @@ int rt_scene_set_launch(rt_scene* s, int32_t variant, int32_t min_active)
     g_err[0] = 0;
     RT_REQ(s, "scene is NULL");
     RT_REQ(variant >= -1 && variant < kVariants, "variant must be -1 (keep) or 0..%d", kVariants - 1);
-    RT_REQ(variant < 0 || variant_compiled(s->desc.precision, s->desc.integrator, variant),
-           "variant %d is not compiled for this precision and integrator", variant);
+    RT_REQ(variant < 0 || variant_compiled(s->desc.precision, render_mode(s->desc), variant),
+           "variant %d is not compiled for this precision, integrator and mirror", variant);
     RT_REQ(variant < 0 || variant == kVariantWave || s->desc.flags == 0,
            "scene options (RT_FLAG_*) are rendered by the wavefront loop (variant %d) only", kVariantWave);
     RT_REQ(min_active == 0 || (min_active >= 1 && min_active <= 32), "min_active must be 0 (keep) or 1..32");
     if (variant >= 0 && variant != s->variant) {
         int bps = 0;
-        RT_CK(render_occupancy(s->desc.precision, s->desc.integrator, variant, s->desc.flags != 0, &bps));
+        RT_CK(render_occupancy(s->desc.precision, render_mode(s->desc), variant, s->desc.flags != 0, &bps));
         RT_REQ(bps > 0, "variant %d does not fit on this device", variant);
         s->variant = variant;
         s->grid = bps * s->nsm;

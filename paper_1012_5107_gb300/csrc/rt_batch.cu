@@ -202,6 +202,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
         int p, g, d;
         if (scene_info(scenes[i], &dev[i], &p, &g, &d) != RT_OK) return RT_EINVAL;
         RT_REQ(dev[i].pix_list == nullptr, "scene %d", i);
+        RT_REQ(dev[i].mirror != RT_MIRROR_GAUSS, "scene %d: scenes of the Gaussian bump are rendered alone", i);
         if (i == 0) { precision = p; integrator = g; device = d; }
         RT_REQ(p == precision && g == integrator, "scenes of a batch must share precision and integrator (scene %d)", i);
         RT_REQ(d == device, "scenes of a batch must live on one device (scene %d)", i);

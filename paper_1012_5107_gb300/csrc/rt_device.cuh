@@ -31,6 +31,14 @@ struct StepConst {
     R fk;        // force factor k s^2 (s: index scale of the cloak, 1 unless referenced)
     R ybot;      // bottom of the box: -A (cloak) or 0 (plate on the flat mirror)
     R is2;       // 1/s^2: the time form's acceleration F/n^2 with F scaled by s^2 and n^2 = s^2 |r|^2
+    // Gaussian bump (RT_MIRROR_GAUSS): width w_b, 1/w_b, k h, h/w_b, Newton
+    // stop |dW|^2 <= gtol, and the largest Newton step |dW|^2 <= gcap2
+    R gw, igw, gkh, gq, gtol, gcap2;
+};
+
+// Hot counters of a lane, kept in registers.
+struct LaneStats {
+    uint32_t steps, evals, newton, refine;
 };
 
 // Constants of the straight segments to the background, in the path's precision.

@@ -19,6 +19,16 @@ constexpr int kVariantWave = 3;
 constexpr int kDefaultVariant = kVariantWave;
 constexpr int kMinActive = 28;   // an integration task continues while at least this many of its 32 rays are inside the cloak
 constexpr int kMaxWindows = 16;
+// Render mode: the integrator (RT_RK4, RT_DP45, RT_RK4T), with kModeGauss set
+// for scenes of the Gaussian bump, whose box holds the Gaussian map's medium.
+constexpr int kModeGauss = 8;
+inline int render_mode(const rt_scene_desc& d)
+{
+    return d.integrator | (d.mirror == RT_MIRROR_GAUSS ? kModeGauss : 0);
+}
+// Coefficients of the Faddeeva series of the Gaussian cloak, uploaded once
+// per device before its first Gaussian scene.
+cudaError_t gauss_upload();
 constexpr int kCounters = 17;      // [0] work counter, [1..11] statistics, [12..15] optional profile,
                                    // [16] wavefront-loop waits that timed out
 
@@ -31,10 +41,10 @@ struct Windows {
     int j0[kMaxWindows], j1[kMaxWindows];
 };
 
-// Whether launch variant `variant` exists for this precision and integrator.
-bool variant_compiled(int precision, int integrator, int variant);
+// Whether launch variant `variant` exists for this precision and render mode.
+bool variant_compiled(int precision, int mode, int variant);
 // opt: the options build of the wavefront loop (scenes with RT_FLAG_* set)
-cudaError_t render_occupancy(int precision, int integrator, int variant, bool opt, int* blocks_per_sm);
+cudaError_t render_occupancy(int precision, int mode, int variant, bool opt, int* blocks_per_sm);
 // Scratch of the wavefront loop for pixels of several samples: 3 floats per
 // sample (col) and one counter per pixel (cnt, zero at launch).
 struct SampleScratch {

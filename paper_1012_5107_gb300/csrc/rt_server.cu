@@ -329,6 +329,10 @@ int rt_submit(rt_server* S, const rt_scene_desc* desc, float* d_out, uint64_t* t
     rt_scene_desc d = *desc;
     const int vr = rt_validate_desc(&d);
     if (vr != RT_OK) return vr;
+    if (d.mirror == RT_MIRROR_GAUSS) {
+        set_error("scenes of the Gaussian bump are rendered alone (rt_render), not served");
+        return RT_EINVAL;
+    }
     Request r;
     r.desc = d;
     r.d_out = d_out;

@@ -33,17 +33,20 @@
 
 #include "rt.h"
 #include "rt_device.cuh"
+#include "rt_gauss.cuh"
 #include "rt_internal.h"
 
 namespace grt {
 
+// The integrator template argument INTEG of the tracer also carries the
+// medium of the box: kModeGauss (rt_internal.h) set selects the Gaussian
+// conformal cloak (rt_gauss.cuh) in place of the grating cloak of Eq. 1.
+__host__ __device__ constexpr int integ_of(int mode) { return mode & 7; }
+__host__ __device__ constexpr bool gauss_of(int mode) { return (mode & kModeGauss) != 0; }
+
 enum : int { PH_IDLE = 0, PH_AIR = 1, PH_BOX = 2, PH_DONE = 3, PH_EXIT = 4, PH_EVENT = 5, PH_GUARD = 6 };
 enum : int { EV_NONE = -1, EV_GRATING = 0, EV_TOP = 1, EV_XP = 2, EV_XM = 3, EV_ZP = 4, EV_ZM = 5, EV_COUNT = 6 };
 
-// Hot counters, kept in registers.
-struct LaneStats {
-    uint32_t steps, evals, newton, refine;
-};
 
 template <class R> struct Branch;
 
@@ -228,6 +231,75 @@ __device__ __forceinline__ void w0_continue(const StepConst<R>& k, R X, R y, R d
 }
 
 // ------------------------------------------------------------------------
+// Medium of the box, by the kind of cloak.  The Box fields (wr, wi) hold W0
+// (grating) or W = -i k (w - z) (Gaussian), (rr, ri) hold dw/dz, (Fx, Fy)
+// the force.
+// ------------------------------------------------------------------------
+// Solve at (X, y) from the guess in (wr, wi); the force too.
+template <class R, int INTEG>
+__device__ __forceinline__ void med_eval(const StepConst<R>& k, R X, R y, R& wr, R& wi, R& rr, R& ri, R& Fx, R& Fy,
+                                         LaneStats& st)
+{
+    if constexpr (gauss_of(INTEG)) {
+        gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, st);
+    } else {
+        w0_eval(k, X, y, wr, wi, rr, ri, st);
+        ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    }
+}
+
+// Solve only: the grating leaves the force to med_force (which it computes
+// from W0 and 1/(1+W0) alone); the Gaussian solve yields it anyway.
+template <class R, int INTEG>
+__device__ __forceinline__ void med_solve(const StepConst<R>& k, R X, R y, R& wr, R& wi, R& rr, R& ri, R& Fx,
+                                          R& Fy, LaneStats& st)
+{
+    if constexpr (gauss_of(INTEG)) gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, st);
+    else w0_eval(k, X, y, wr, wi, rr, ri, st);
+}
+
+template <class R, int INTEG>
+__device__ __forceinline__ void med_force(const StepConst<R>& k, Box<R>& b)
+{
+    if constexpr (!gauss_of(INTEG)) ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
+}
+
+// A stage point (X, y) reached by (dx, dy) from the previous point, whose
+// values are in (wr, wi, rr, ri) and (Fpx, Fpy): continuation and solve; the
+// force at the new point goes to (Fx, Fy).
+template <class R, int INTEG>
+__device__ __forceinline__ void med_stage(const StepConst<R>& k, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri,
+                                          R Fpx, R Fpy, R& Fx, R& Fy, LaneStats& st)
+{
+    if constexpr (gauss_of(INTEG)) {
+        gauss_predict(wr, wi, rr, ri, Fpx, Fpy, dx, dy);
+        gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, st);
+    } else {
+        w0_continue(k, X, y, dx, dy, wr, wi, rr, ri, st);
+        ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    }
+}
+
+// Continuation only (the guess for the solve at the end of a step).
+template <class R, int INTEG>
+__device__ __forceinline__ void med_predict(R& wr, R& wi, R rr, R ri, R Fx, R Fy, R dx, R dy)
+{
+    if constexpr (gauss_of(INTEG)) gauss_predict(wr, wi, rr, ri, Fx, Fy, dx, dy);
+    else w0_predict(wr, wi, rr, ri, dx, dy);
+}
+
+// Keep the grating's abscissa as cell + fraction; the Gaussian box works
+// with the absolute abscissa (cx = 0).
+template <class R, int INTEG>
+__device__ __forceinline__ void wrap_cell(Box<R>& o)
+{
+    if constexpr (!gauss_of(INTEG)) {
+        if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
+        else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+    }
+}
+
+// ------------------------------------------------------------------------
 // RK4 in the cloak.
 // ------------------------------------------------------------------------
 template <class R>
@@ -245,26 +317,23 @@ __device__ __forceinline__ void kahan_add(R& s, R& c, R inc)
 
 // One RK4 step of size h from s (W0 solved and force known at s) into o;
 // o's W0 is continued to the end point but not solved.
-template <class R>
+template <class R, int INTEG>
 __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
 {
     const R h2 = R(0.5) * h;
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     // stage 2 at r + h/2 p
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
-    w0_continue(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
     R F2x, F2y;
-    ray_force(wr, wi, rr, ri, k.fk, F2x, F2y);
+    med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, F2x, F2y, st);
     // stage 3 at r + h/2 (p + h/2 F1), (h/2)^2 F1 away from stage 2
     const R X3 = s.X + h2 * (s.px + h2 * s.Fx), y3 = s.y + h2 * (s.py + h2 * s.Fy);
-    w0_continue(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
     R F3x, F3y;
-    ray_force(wr, wi, rr, ri, k.fk, F3x, F3y);
+    med_stage<R, INTEG>(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, F2x, F2y, F3x, F3y, st);
     // stage 4 at r + h (p + h/2 F2)
     const R X4 = s.X + h * (s.px + h2 * F2x), y4 = s.y + h * (s.py + h2 * F2y);
-    w0_continue(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
     R F4x, F4y;
-    ray_force(wr, wi, rr, ri, k.fk, F4x, F4y);
+    med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, F3x, F3y, F4x, F4y, st);
     // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
     const R h6 = h * R(1.0 / 6.0), hh6 = h * h6;
     const R dX = h * s.px + hh6 * (s.Fx + F2x + F3x);
@@ -278,10 +347,9 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     kahan_add(o.z, o.cz, dZ);
     kahan_add(o.px, o.cpx, dPx);
     kahan_add(o.py, o.cpy, dPy);
-    w0_predict(wr, wi, rr, ri, o.X - X4, o.y - y4);
+    med_predict<R, INTEG>(wr, wi, rr, ri, F4x, F4y, o.X - X4, o.y - y4);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
-    if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
-    else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+    wrap_cell<R, INTEG>(o);
 }
 
 // ------------------------------------------------------------------------
@@ -307,7 +375,7 @@ __device__ __forceinline__ void accel_t(const StepConst<R>& k, R Fx, R Fy, R vx,
 // (r, v)' = (v, a(r, v)) from s (W0 solved and F known at s) into o; o's W0
 // is continued to the end point but not solved.  v_z changes along the ray
 // (n^2 v_z is the conserved momentum) and is summed without compensation.
-template <class R>
+template <class R, int INTEG>
 __device__ __forceinline__ void rk4t_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
 {
     const R h2 = R(0.5) * h;
@@ -318,22 +386,19 @@ __device__ __forceinline__ void rk4t_step(const StepConst<R>& k, const Box<R>& s
     // stage 2 at (r + h/2 v, v + h/2 a1)
     const R v2x = s.px + h2 * a1x, v2y = s.py + h2 * a1y, v2z = s.pz + h2 * a1z;
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
-    w0_continue(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, st);
-    ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, Fx, Fy, st);
     R a2x, a2y, a2z;
     accel_t(k, Fx, Fy, v2x, v2y, v2z, rr, ri, a2x, a2y, a2z);
     // stage 3 at (r + h/2 v2, v + h/2 a2)
     const R v3x = s.px + h2 * a2x, v3y = s.py + h2 * a2y, v3z = s.pz + h2 * a2z;
     const R X3 = s.X + h2 * v2x, y3 = s.y + h2 * v2y;
-    w0_continue(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, st);
-    ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    med_stage<R, INTEG>(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, Fx, Fy, Fx, Fy, st);
     R a3x, a3y, a3z;
     accel_t(k, Fx, Fy, v3x, v3y, v3z, rr, ri, a3x, a3y, a3z);
     // stage 4 at (r + h v3, v + h a3)
     const R v4x = s.px + h * a3x, v4y = s.py + h * a3y, v4z = s.pz + h * a3z;
     const R X4 = s.X + h * v3x, y4 = s.y + h * v3y;
-    w0_continue(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, st);
-    ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
+    med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, Fx, Fy, Fx, Fy, st);
     R a4x, a4y, a4z;
     accel_t(k, Fx, Fy, v4x, v4y, v4z, rr, ri, a4x, a4y, a4z);
     // increments h/6 (k1 + 2 k2 + 2 k3 + k4) of both halves of the state
@@ -351,10 +416,9 @@ __device__ __forceinline__ void rk4t_step(const StepConst<R>& k, const Box<R>& s
     kahan_add(o.px, o.cpx, dVx);
     kahan_add(o.py, o.cpy, dVy);
     o.pz += dVz;
-    w0_predict(wr, wi, rr, ri, o.X - X4, o.y - y4);
+    med_predict<R, INTEG>(wr, wi, rr, ri, Fx, Fy, o.X - X4, o.y - y4);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
-    if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
-    else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+    wrap_cell<R, INTEG>(o);
 }
 
 // Dormand & Prince (1980) RK5(4)7M: nodes, coefficients, fifth-order weights
@@ -445,7 +509,7 @@ template <> __device__ __forceinline__ double dp_tab_c<double>(int r) { return k
 // r + c_j h p + h^2 sum_l (A A)_jl F_l, the solution
 // r + h p + h^2 sum_l (b A)_l F_l and p + h sum_j b_j F_j, and the position
 // error h^2 sum_l (e A)_l F_l -- the same method with only the forces kept.
-template <class R>
+template <class R, int INTEG>
 __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
                                           LaneStats& st)
 {
@@ -485,8 +549,8 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
             Xs = o.X;
             Ys = o.y;
         }
-        w0_continue(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, st);
-        ray_force(wr, wi, rr, ri, k.fk, Fx[j - 1], Fy[j - 1]);
+        med_stage<R, INTEG>(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, Fx[j - 2], Fy[j - 2], Fx[j - 1], Fy[j - 1],
+                            st);
         Xp = Xs;
         yp = Ys;
     }
@@ -507,8 +571,7 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
     e[1] = hh * ey;
     e[2] = h * gx;
     e[3] = h * gy;
-    if (o.X >= R(0.5)) { o.X -= R(1); o.cx += R(1); }
-    else if (o.X < R(-0.5)) { o.X += R(1); o.cx -= R(1); }
+    wrap_cell<R, INTEG>(o);
 }
 
 // One step of the scene's integrator of size h from s into o (for event
@@ -516,13 +579,13 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
 template <class R, int INTEG>
 __device__ __forceinline__ void integ_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
 {
-    if constexpr (INTEG == RT_DP45) {
+    if constexpr (integ_of(INTEG) == RT_DP45) {
         R e[4];
-        dp45_step(k, s, h, o, e, st);
-    } else if constexpr (INTEG == RT_RK4T) {
-        rk4t_step(k, s, h, o, st);
+        dp45_step<R, INTEG>(k, s, h, o, e, st);
+    } else if constexpr (integ_of(INTEG) == RT_RK4T) {
+        rk4t_step<R, INTEG>(k, s, h, o, st);
     } else {
-        rk4_step(k, s, h, o, st);
+        rk4_step<R, INTEG>(k, s, h, o, st);
     }
 }
 
@@ -609,7 +672,7 @@ __device__ R locate_event(const StepConst<R>& k, const Box<R>& b, R h, int ev, b
     int side = 0;
     for (int it = 0; it < Mth<R>::kEventIt; ++it) {
         integ_step<R, INTEG>(k, b, th * h, t, st);
-        w0_eval(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
+        med_solve<R, INTEG>(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, t.Fx, t.Fy, st);
         const R g = event_g(k, ev, t);
         if (fabs(g) <= Mth<R>::kEventTol) return th;
         const R gd = on_surface ? g / th : g;
@@ -807,6 +870,96 @@ __device__ R trochoid_line_hit(const StepConst<R>& k, const Cold<R>& C, bool on_
         fy += u_b * dy;
         ha = hb;
     }
+    return R(INFINITY);
+}
+
+// First hit of the line with the Gaussian bump, or infinity.  As for the
+// trochoid, the part of the line in the band 0 <= y <= h is marched, in
+// increments of w_b/8 in the xy-plane, and the first increment ending at or
+// below the surface is refined by Illinois; the abscissa is absolute.  Only
+// the core |x| <= 10 w_b + h is marched: beyond it the bump lies below
+// h exp(-100), and a descending line meets the surface where it reaches
+// y = 0.  On a hit the hit point is returned in (hcx, hX, hy).
+template <class R>
+__device__ R bump_line_hit(const StepConst<R>& k, const Cold<R>& C, bool on_surface, R& hcx, R& hX, R& hy)
+{
+    const R A = k.A;
+    const R dx = C.dx, dy = C.dy;
+    const R dxy = Mth<R>::sqrt_(dx * dx + dy * dy);
+    if (!(dxy > R(1e-30))) return R(INFINITY);
+    if (dy >= R(0) && C.y >= A) return R(INFINITY);
+    R t0 = R(0), x0 = C.cx + C.X, y0 = C.y;
+    if (C.y > A) {
+        t0 = (A - C.y) / dy;
+        x0 += t0 * dx;
+        y0 = A;
+    }
+    const R xc = R(10) * k.gw + A;
+    R L;
+    if (dy < R(0)) L = -y0 / dy;
+    else if (dy > R(0)) L = (A - y0) / dy;
+    else L = (fabs(x0) + xc) / fabs(dx);
+    if (!(L >= R(0))) L = R(0);
+    // the part [va, vb] of [0, L] over the core
+    R va = R(0), vb = L;
+    if (dx != R(0)) {
+        const R v1 = (-xc - x0) / dx, v2 = (xc - x0) / dx;
+        va = fmax(va, fmin(v1, v2));
+        vb = fmin(vb, fmax(v1, v2));
+    } else if (fabs(x0) > xc) {
+        vb = R(-1);
+    }
+    auto set_hit = [&](R v) {
+        const R x = x0 + v * dx;
+        const R m = Mth<R>::rint_(x);
+        hcx = m;
+        hX = x - m;
+        hy = y0 + v * dy;
+        return t0 + v;
+    };
+    auto height = [&](R v) -> R { return bump_height(k, x0 + v * dx, y0 + v * dy); };
+    if (va < vb) {
+        const R ds = R(0.125) * k.gw / dxy;
+        bool first = on_surface && t0 == R(0) && va == R(0);
+        R s_a = va, ha;
+        if (first) {
+            R tx, ty;
+            bump_tangent(k, bump_u(k, x0), tx, ty);
+            ha = dy - (ty / tx) * dx;
+            if (!(ha > R(0))) ha = R(1e-30);
+        } else {
+            ha = height(s_a);
+            if (ha <= R(0)) return set_hit(s_a);
+        }
+        for (int guard = 0; guard < (1 << 20); ++guard) {
+            R u_b = fmin(ds, vb - s_a);
+            if (first && u_b <= Mth<R>::kRehit) {
+                if (s_a + u_b >= vb) break;
+                u_b = fmin(Mth<R>::kRehit, vb - s_a);
+            }
+            if (!(u_b >= R(0))) break;
+            const bool last = !(s_a + u_b < vb);
+            R hb = height(s_a + u_b);
+            if (last && vb == L && dy < R(0) && hb > R(0)) hb = R(0);   // the line reaches y = 0 here
+            if (hb <= R(0)) {
+                R u;
+                if (first) {
+                    auto defl = [&](R v) -> R { return height(s_a + v) / v; };
+                    u = (u_b > R(0)) ? illinois_root(defl, R(0), ha, u_b, hb / u_b) : R(0);
+                } else {
+                    auto hf = [&](R v) -> R { return height(s_a + v); };
+                    u = (u_b > R(0)) ? illinois_root(hf, R(0), ha, u_b, hb) : R(0);
+                }
+                return set_hit(s_a + u);
+            }
+            if (last) break;
+            first = false;
+            s_a += u_b;
+            ha = hb;
+        }
+    }
+    // no hit over the core: a descending line meets the flat part at y = 0
+    if (dy < R(0) && !(on_surface && t0 == R(0) && L <= Mth<R>::kRehit)) return set_hit(L);
     return R(INFINITY);
 }
 
@@ -1010,7 +1163,11 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
     for (;;) {
         if (C.bounces > sc.max_bounces) { finish_sample<R, OPT>(sc, C, steps, RT_RAY_MAX_BOUNCES, phase, rec); return; }
         R hcx = R(0), hX = R(0), hy = R(0);
-        const R tm = sc.mirror ? trochoid_line_hit(k, C, surf == EV_GRATING, hcx, hX, hy) : flat_line_hit(C);
+        R tm;
+        if constexpr (gauss_of(INTEG))
+            tm = sc.mirror ? bump_line_hit(k, C, surf == EV_GRATING, hcx, hX, hy) : flat_line_hit(C);
+        else
+            tm = sc.mirror ? trochoid_line_hit(k, C, surf == EV_GRATING, hcx, hX, hy) : flat_line_hit(C);
         int face = EV_NONE;
         const R tb = (sc.cloak || plate) ? box_entry(k, C, face) : R(INFINITY);
         if (tb < tm) {
@@ -1039,10 +1196,14 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             }
             b.cx = C.cx;
             b.X = C.X;
+            if constexpr (gauss_of(INTEG)) {  // the Gaussian box works with the absolute abscissa
+                b.cx = R(0);
+                b.X = C.cx + C.X;
+            }
             b.y = C.y;
             b.z = C.z;
             b.wr = b.wi = R(0);
-            w0_eval(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
+            med_solve<R, INTEG>(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy, st);
             // Snell's law in FP64 (a few operations per entry): sqrt(n^2 - |p_t|^2)
             // is ill-conditioned near grazing incidence; the index is scaled
             // by idx_scale in the referenced cloak
@@ -1062,13 +1223,13 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                 fresnel_split(C, fresnel_R(1.0, sqrt(n2), pn, pin), MED_AIR, C.cx, C.X, C.y, C.z,
                               d[0] - 2.0 * pn * N[0], d[1] - 2.0 * pn * N[1], d[2] - 2.0 * pn * N[2], EV_NONE, steps);
             // the momentum |p| = n inside; the time form carries v = p / n^2
-            const double iv = (INTEG == RT_RK4T) ? 1.0 / n2 : 1.0;
+            const double iv = (integ_of(INTEG) == RT_RK4T) ? 1.0 / n2 : 1.0;
             b.px = (R)((pt[0] - pin * N[0]) * iv);
             b.py = (R)((pt[1] - pin * N[1]) * iv);
             b.pz = (R)((pt[2] - pin * N[2]) * iv);
             b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
             b.hc = k.h;
-            ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
+            med_force<R, INTEG>(k, b);
             surf = face;
             phase = PH_BOX;
             return;
@@ -1079,11 +1240,21 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                 C.cx = hcx;
                 C.X = hX;
                 C.y = hy;
-                // upward normal from the tangent of Eq. 2 at the phase of the hit
-                const R E = trochoid_phase(C.X, k.kA);
-                R sn, cs;
-                Mth<R>::sincos(E, sn, cs);
-                const double nx = (double)k.kA * (double)sn, ny = 1.0 - (double)k.kA * (double)cs;
+                // upward normal from the tangent of Eq. 2 at the phase of the
+                // hit (of the bump's parametric form for the Gaussian bump)
+                double nx, ny;
+                if constexpr (gauss_of(INTEG)) {
+                    R tx, ty;
+                    bump_tangent(k, bump_u(k, C.cx + C.X), tx, ty);
+                    nx = -(double)ty;
+                    ny = (double)tx;
+                } else {
+                    const R E = trochoid_phase(C.X, k.kA);
+                    R sn, cs;
+                    Mth<R>::sincos(E, sn, cs);
+                    nx = (double)k.kA * (double)sn;
+                    ny = 1.0 - (double)k.kA * (double)cs;
+                }
                 const double il = 1.0 / sqrt(nx * nx + ny * ny);
                 const double pn = ((double)C.dx * nx + (double)C.dy * ny) * il;
                 C.dx = (R)((double)C.dx - 2.0 * pn * nx * il);
@@ -1136,12 +1307,12 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     }
     if (last != ev_best) {
         integ_step<R, INTEG>(k, b, th_best * C.hs, t, st);
-        w0_eval(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, st);
+        med_solve<R, INTEG>(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, t.Fx, t.Fy, st);
     }
     const R hc = b.hc;
     b = t;
     b.hc = hc;
-    ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
+    med_force<R, INTEG>(k, b);
     C.events++;
     C.nevents++;
     if (ev_best == EV_GRATING) {
@@ -1168,7 +1339,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     R Nf[3];
     face_normal(ev_best, Nf);
     double n2f = 1.0;
-    if constexpr (INTEG == RT_RK4T)
+    if constexpr (integ_of(INTEG) == RT_RK4T)
         n2f = ((double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri) / (double)k.is2;
     const double p[3] = {(double)b.px * n2f, (double)b.py * n2f, (double)b.pz * n2f};
     const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
@@ -1204,6 +1375,11 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     const double il = 1.0 / sqrt(l2);
     C.cx = b.cx;
     C.X = b.X;
+    if constexpr (gauss_of(INTEG)) {          // back to cell + fraction in air
+        const R m = Mth<R>::rint_(b.X);
+        C.cx = m;
+        C.X = b.X - m;
+    }
     C.y = b.y;
     C.z = b.z;
     C.dx = (R)(d[0] * il);
@@ -1231,12 +1407,12 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         return;
     }
     R hs;
-    if constexpr (INTEG == RT_DP45) {
+    if constexpr (integ_of(INTEG) == RT_DP45) {
         // one attempt of an adaptive Dormand-Prince step; a rejected attempt
         // only shrinks the step
         hs = s.hc;
         R e[4];
-        dp45_step(k, s, hs, o, e, st);
+        dp45_step<R, INTEG>(k, s, hs, o, e, st);
         ++steps;
         st.steps++;
         const R scp = k.atol + k.rtol;                                    // positions (units of Lambda)
@@ -1271,10 +1447,9 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         o.hc = fmin(hs * fac, k.hmax);
     } else {
         hs = k.h;
-        if constexpr (INTEG == RT_RK4T) rk4t_step(k, s, hs, o, st);
-        else rk4_step(k, s, hs, o, st);
-        w0_eval(k, o.X, o.y, o.wr, o.wi, o.rr, o.ri, st);
-        ray_force(o.wr, o.wi, o.rr, o.ri, k.fk, o.Fx, o.Fy);
+        if constexpr (integ_of(INTEG) == RT_RK4T) rk4t_step<R, INTEG>(k, s, hs, o, st);
+        else rk4_step<R, INTEG>(k, s, hs, o, st);
+        med_eval<R, INTEG>(k, o.X, o.y, o.wr, o.wi, o.rr, o.ri, o.Fx, o.Fy, st);
         ++steps;
         st.steps++;
     }
@@ -1294,7 +1469,7 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
     C.g1[EV_ZP] = gZp;
     C.g1[EV_ZM] = gZm;
     C.hs = hs;
-    if constexpr (INTEG == RT_DP45) s.hc = o.hc;
+    if constexpr (integ_of(INTEG) == RT_DP45) s.hc = o.hc;
     phase = PH_EVENT;
 }
 
@@ -1366,9 +1541,9 @@ __device__ void start_branch(const DevScene& sc, Cold<R>& C, Box<R>& b, int& pha
         b.pz = q.p[2];
         b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
         b.wr = b.wi = R(0);
-        w0_eval(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, st);
-        ray_force(b.wr, b.wi, b.rr, b.ri, k.fk, b.Fx, b.Fy);
-        if constexpr (INTEG == RT_RK4T) {
+        med_solve<R, INTEG>(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy, st);
+        med_force<R, INTEG>(k, b);
+        if constexpr (integ_of(INTEG) == RT_RK4T) {
             // the branch holds the momentum; the time form carries v = p / n^2
             const double iv = (double)k.is2 / ((double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri);
             b.px = (R)((double)q.p[0] * iv);

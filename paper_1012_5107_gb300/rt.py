@@ -33,6 +33,7 @@ class SceneDesc(C.Structure):
         ("bg_cell", C.c_double), ("tex_texel", C.c_double),
         ("colour0", C.c_double * 3), ("colour1", C.c_double * 3),
         ("h", C.c_double), ("rtol", C.c_double), ("atol", C.c_double), ("h_max", C.c_double),
+        ("gauss_w", C.c_double),
         ("seed", C.c_uint64), ("scene_id", C.c_uint64),
         ("max_steps", C.c_int64),
         ("tex", C.POINTER(C.c_float)),

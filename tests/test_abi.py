@@ -52,6 +52,8 @@ def test_version(rt):
     (dict(precision=3), "precision"), (dict(background=1, tex_size=0), "texture"),
     (dict(mirror=0, cloak=1), "trochoid"), (dict(flags=8), "unknown bits"), (dict(max_steps=0), "max_steps"),
     (dict(flags=2), "plate lies on the flat mirror"),
+    (dict(mirror=2, A=0.3, gauss_w=0.306, H=1.1), "0.8 gauss_w"), (dict(mirror=2, gauss_w=0.0), "gauss_w"),
+    (dict(mirror=2, A=0.13, gauss_w=0.306, H=1.1, flags=4), "no options"), (dict(mirror=3), "mirror must"),
 ])
 def test_invalid_descriptor_is_rejected(rt, bad, field):
     p = inputs.base_scene(**bad)
@@ -86,6 +88,7 @@ def test_struct_layouts_match_header(rt, tmp_path):
 def test_validate_desc_on_host(rt):
     rt.validate(inputs.base_scene())
     rt.validate(inputs.base_scene(integrator=2))          # RK4 in physical time (Eq. 11)
+    rt.validate(inputs.gauss_scene())                     # the Gaussian conformal cloak (Fig. 4)
     with pytest.raises(rt.RtError) as e:
         rt.validate(inputs.base_scene(spp=0))
     assert e.value.code == rt.RT_EINVAL

@@ -44,7 +44,7 @@ MUFU_PER_NEWTON = 4
 # renders): dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture
 # (--set full, one launch) of the current kernel; None until that capture
 # exists or after the kernel changes.
-TRAFFIC_BATCH_BYTES = 9463808
+TRAFFIC_BATCH_BYTES = 10431232
 
 
 def peaks():
@@ -329,6 +329,7 @@ def run_gpu(args):
     table1 = None if args.no_table1 else bench_table1(rt, torch, stream)
     hd = None if args.no_hd else bench_hd(rt, torch, stream)
     tform = None if args.no_time_form else bench_time_form(rt, torch, stream)
+    gauss = None if args.no_gauss else bench_gauss_fig4(rt, torch, stream)
     batch = None if args.no_batch else bench_batch(rt, torch, stream)
     serving = None if args.no_serving else bench_serving(rt, torch)
 
@@ -358,6 +359,7 @@ def run_gpu(args):
         "table1_referenced_fresnel": table1,
         "hd_dp45_1920x1080x16": hd,
         "time_form_eq11_cloak_render": tform,
+        "gaussian_cloak_fig4": gauss,
         "batched_64_scenes": batch,
         "serving": serving,
         "gpu_launches": step.launches * args.steps,
@@ -506,6 +508,46 @@ def bench_time_form(rt, torch, stream) -> dict:
     return out
 
 
+def bench_gauss_fig4(rt, torch, stream) -> dict:
+    """The Gaussian conformal cloak of Fig. 1(b) and Fig. 4 (w = 0.306,
+    h = 0.13, box 1.1 high), 512 x 512 x 4 in FP32: the flat mirror, the bare
+    and the cloaked bump and their centre lines; C(0,0) of the mirror against
+    the bare and the cloaked bump at FOV 0/10/25/50 deg (the Gaussian rows of
+    Table 1); the cloaked render timed over three launches after a warm-up."""
+    base = inputs.gauss_scene(width=SIDE, height=SIDE, spp=SPP, seed=2, precision=inputs.FP32)
+    imgs, scenes = {}, {}
+    for kind, p in inputs.gauss_renders(base).items():
+        for line in (0, 1):
+            key = kind + ("_line" if line else "")
+            scenes[key] = rt.Scene(dict(p, centre_line=line))
+            imgs[key] = torch.zeros(scenes[key].shape, dtype=torch.float32, device="cuda")
+            with torch.cuda.stream(stream):
+                scenes[key].render(imgs[key], stream=stream)
+    torch.cuda.synchronize()
+    sc = scenes["cloak"]
+    n = 3
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(stream):
+        e0.record(stream)
+        for _ in range(n):
+            sc.render(imgs["cloak"], stream=stream)
+        e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / n
+    st = sc.stats()
+    out = {"cloak_ms": round(ms, 3), "Mrays_per_s": round(st["rays"] / (ms * 1e-3) / 1e6, 3),
+           "Gsteps_per_s": round(st["steps"] / (ms * 1e-3) / 1e9, 4),
+           "steps_per_ray": round(st["steps"] / st["rays"], 1)}
+    for other in ("bare", "cloak"):
+        c = rt.xcorr(imgs["mirror"], imgs[other], [10.0, 25.0, 50.0], 50.0).cpu().numpy()
+        c0 = rt.xcorr(imgs["mirror_line"], imgs[other + "_line"], [50.0], 50.0).cpu().numpy()
+        out[f"C_mirror_vs_{other}"] = {"0": round(float(c0[0, 3]), 4), "10": round(float(c[0, 3]), 4),
+                                       "25": round(float(c[1, 3]), 4), "50": round(float(c[2, 3]), 4)}
+    for s_ in scenes.values():
+        s_.close()
+    return out
+
+
 def bench_batch(rt, torch, stream) -> dict:
     """64 scenes drawn from seed 4 (sides 128..1024, spp 1/4/16, A, Lambda,
     elevation and azimuth random) in one persistent launch replayed from a
@@ -644,6 +686,7 @@ def main():
     ap.add_argument("--no-table1", action="store_true")
     ap.add_argument("--no-hd", action="store_true")
     ap.add_argument("--no-time-form", action="store_true")
+    ap.add_argument("--no-gauss", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

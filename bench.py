@@ -33,12 +33,22 @@ FOVS = [0.0, 10.0, 25.0, 50.0]
 SIDE, SPP = 512, 4
 WORKLOAD = "grating cloak 512x512 4spp RK4 h=L/200, mirror+bare+cloak + centre lines + C(0,0) at 0/10/25/50 deg"
 
-# Algorithmic FP32 operations (FMA = 2) per unit of work of the render kernel;
-# the counters of one launch give the units (see the kernel's w0_solve,
-# ray_force, w0_predict and rk4_step).
-FLOP_PER_NEWTON = 33     # one Newton step on W + kA exp(-(W - ikz)) = 0 (rcp, ex2, sin, cos on MUFU)
-FLOP_PER_EVAL = 53       # continuation of W0, update of 1/(1+W0), force k n^2 (Im, Re) W r^2
-FLOP_PER_STEP = 105      # RK4 stage points, increments, compensated sums, event functions
+# Algorithmic work per RK4 ray-step (the unit of the roofline): 4 index
+# evaluations of (45 + 30 I) FLOP and (2 + 4 I) MUFU operations each (zeta,
+# I Halley iterations for W0, the gradient), plus 40 FLOP of state update,
+# with I the oracle's mean number of Halley iterations per evaluation (cold
+# start at every evaluation), measured by `python oracle/mean_halley.py
+# --pixels 2000` on the cloaked render: I = 3.9772.  Fixed constants, not the
+# kernel's own counters: its warm-started Newton solve does less work.
+ORACLE_MEAN_I = 3.9772
+FLOP_PER_RAY_STEP = 4 * (45 + 30 * ORACLE_MEAN_I) + 40
+MUFU_PER_RAY_STEP = 4 * (2 + 4 * ORACLE_MEAN_I)
+# What the kernel executes, from its counters (FMA = 2): per Newton step on
+# W + kA exp(-(W - ikz)) = 0, per evaluation (continuation, 1/(1+W0), force)
+# and per RK4 step (stage points, increments, compensated sums, events).
+FLOP_PER_NEWTON = 33
+FLOP_PER_EVAL = 53
+FLOP_PER_STEP = 105
 MUFU_PER_NEWTON = 4
 # DRAM bytes (read + write) of one batched render launch of the step (the six
 # renders): dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture
@@ -247,19 +257,24 @@ def run_gpu(args):
 
     # roofline of the dominant kernel: the batched render of the step
     bst = stats
-    flop = FLOP_PER_NEWTON * bst["newton"] + FLOP_PER_EVAL * bst["evals"] + FLOP_PER_STEP * bst["steps"]
     rn_ms = float(np.mean(render_ms))
     pk, pk_kind = peaks()
     clock_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak_tflops = 152 * 128 * 2 * clock_mhz * 1e6 / 1e12
-    achieved = flop / (rn_ms * 1e-3) / 1e12
-    mufu = MUFU_PER_NEWTON * bst["newton"]
     mufu_peak = 152 * 16 * clock_mhz * 1e6
+    achieved = FLOP_PER_RAY_STEP * bst["steps"] / (rn_ms * 1e-3) / 1e12
+    executed = (FLOP_PER_NEWTON * bst["newton"] + FLOP_PER_EVAL * bst["evals"]
+                + FLOP_PER_STEP * bst["steps"]) / (rn_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": round(achieved, 3), "peak": round(peak_tflops, 2),
                 "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4), "traffic": TRAFFIC_BATCH_BYTES,
                 "kernel": "wave_batch_kernel<float, RK4> (the six renders of the step)",
+                "algorithmic": f"{FLOP_PER_RAY_STEP:.1f} FLOP and {MUFU_PER_RAY_STEP:.1f} MUFU per RK4 ray-step "
+                               f"(oracle mean I = {ORACLE_MEAN_I}) x {bst['steps']} ray-steps per launch",
                 "peak_source": f"derived: 152 SM x 128 FP32 lanes x 2 x {clock_mhz:.0f} MHz (max clock of {pk_kind} peaks file)",
-                "mufu_frac": round(mufu / (rn_ms * 1e-3) / mufu_peak, 4),
+                "mufu_frac": round(MUFU_PER_RAY_STEP * bst["steps"] / (rn_ms * 1e-3) / mufu_peak, 4),
+                "executed_tflops": round(executed, 3),
+                "executed_frac": round(executed / peak_tflops, 4),
+                "executed_mufu_frac": round(MUFU_PER_NEWTON * bst["newton"] / (rn_ms * 1e-3) / mufu_peak, 4),
                 "kernel_ms": round(rn_ms, 3)}
 
     # the cloaked-grating render alone (one launch of the wavefront loop), FP32

@@ -166,6 +166,14 @@ using namespace grt;
 
 struct rt_batch {
     int n, device, precision, integrator, grid, nsm, min_active;
+    // The kernel's work list takes the scenes in slot order: slot j holds the
+    // caller's scene order[j].  Cloaked scenes (rays that integrate) come
+    // first, then bare gratings, then flat mirrors; within a kind the scene
+    // with fewer samples first.  A scene's samples then start early enough
+    // that its longest rays do not make the launch's tail: a centre line of
+    // a cloaked render, taken after a million samples of cheap renders,
+    // would.  The cheap air-only renders fill the end of the launch.
+    std::vector<int> order;
     int64_t total, total_samples;
     DevScene* d_scenes;
     int64_t* d_offsets;      // first pixel of each scene
@@ -193,23 +201,34 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     RT_REQ(out, "out is NULL");
     *out = nullptr;
     RT_REQ(scenes && n >= 1, "need at least one scene");
-    std::vector<DevScene> dev(n);
+    std::vector<DevScene> user(n), dev(n);
     std::vector<int64_t> off(n + 1, 0), soff(n + 1, 0);
     int precision = -1, integrator = -1, device = -1;
     bool fresnel = false, opt = false;
     for (int i = 0; i < n; ++i) {
         RT_REQ(scenes[i], "scene %d is NULL", i);
         int p, g, d;
-        if (scene_info(scenes[i], &dev[i], &p, &g, &d) != RT_OK) return RT_EINVAL;
-        RT_REQ(dev[i].pix_list == nullptr, "scene %d", i);
-        RT_REQ(dev[i].mirror != RT_MIRROR_GAUSS, "scene %d: scenes of the Gaussian bump are rendered alone", i);
+        if (scene_info(scenes[i], &user[i], &p, &g, &d) != RT_OK) return RT_EINVAL;
+        RT_REQ(user[i].pix_list == nullptr, "scene %d", i);
+        RT_REQ(user[i].mirror != RT_MIRROR_GAUSS, "scene %d: scenes of the Gaussian bump are rendered alone", i);
         if (i == 0) { precision = p; integrator = g; device = d; }
         RT_REQ(p == precision && g == integrator, "scenes of a batch must share precision and integrator (scene %d)", i);
         RT_REQ(d == device, "scenes of a batch must live on one device (scene %d)", i);
-        off[i + 1] = off[i] + dev[i].nwork;
-        soff[i + 1] = soff[i] + dev[i].nwork * dev[i].spp;
-        fresnel = fresnel || (dev[i].flags & RT_FLAG_FRESNEL);
-        opt = opt || dev[i].flags != 0;
+        fresnel = fresnel || (user[i].flags & RT_FLAG_FRESNEL);
+        opt = opt || user[i].flags != 0;
+    }
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int c) {
+        const DevScene &x = user[a], &y = user[c];
+        if (x.cloak != y.cloak) return x.cloak > y.cloak;
+        if (x.mirror != y.mirror) return x.mirror > y.mirror;
+        return x.nwork * x.spp < y.nwork * y.spp;
+    });
+    for (int j = 0; j < n; ++j) {
+        dev[j] = user[order[j]];
+        off[j + 1] = off[j] + dev[j].nwork;
+        soff[j + 1] = soff[j] + dev[j].nwork * dev[j].spp;
     }
     int cur = -1;
     RT_CK(cudaGetDevice(&cur));
@@ -217,6 +236,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     rt_batch* b = new (std::nothrow) rt_batch();
     if (!b) { set_error("host allocation failed"); return RT_ENOMEM; }
     b->n = n;
+    b->order = order;
     b->device = device;
     b->precision = precision;
     b->integrator = integrator;
@@ -286,19 +306,21 @@ int rt_batch_update(rt_batch* b, const rt_scene_desc* descs, int32_t n, void* st
     RT_REQ(b && descs, "batch and descs must not be NULL");
     RT_REQ(n == b->n, "the batch holds %d scenes, got %d descriptors", b->n, n);
     std::vector<DevScene> dev(n);
-    for (int i = 0; i < n; ++i) {
+    for (int j = 0; j < n; ++j) {
+        const int i = b->order[j];           // the caller's index of slot j
         if (rt_validate_desc(&descs[i]) != RT_OK) return RT_EINVAL;
-        const DevScene& old = b->h_scenes[i];
-        build_scene_table(&descs[i], &dev[i]);
+        const DevScene& old = b->h_scenes[j];
+        build_scene_table(&descs[i], &dev[j]);
         RT_REQ(descs[i].precision == b->precision && descs[i].integrator == b->integrator,
                "scene %d: precision and integrator must stay", i);
-        RT_REQ(dev[i].nwork == old.nwork && dev[i].spp == old.spp && dev[i].wout == old.wout,
+        RT_REQ(dev[j].nwork == old.nwork && dev[j].spp == old.spp && dev[j].wout == old.wout,
                "scene %d: image size and samples per pixel must stay", i);
-        RT_REQ(dev[i].background == old.background && dev[i].flags == old.flags,
-               "scene %d: background kind and flags must stay", i);
-        dev[i].tex = old.tex;
-        dev[i].tex_size = old.tex_size;
-        dev[i].pix_list = nullptr;
+        RT_REQ(dev[j].background == old.background && dev[j].flags == old.flags &&
+                   dev[j].cloak == old.cloak && dev[j].mirror == old.mirror,
+               "scene %d: background kind, flags, mirror and cloak must stay", i);
+        dev[j].tex = old.tex;
+        dev[j].tex_size = old.tex_size;
+        dev[j].pix_list = nullptr;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = sizeof(DevScene) * (size_t)n;
@@ -323,9 +345,9 @@ int rt_batch_render(rt_batch* b, float* const* d_rgb, void* stream)
     cudaStream_t st = (cudaStream_t)stream;
     // a change of output images is a small upload outside the graph
     bool changed = false;
-    for (int i = 0; i < b->n; ++i) changed = changed || (b->h_rgbs[i] != d_rgb[i]);
+    for (int j = 0; j < b->n; ++j) changed = changed || (b->h_rgbs[j] != d_rgb[b->order[j]]);
     if (changed) {
-        for (int i = 0; i < b->n; ++i) b->h_rgbs[i] = d_rgb[i];
+        for (int j = 0; j < b->n; ++j) b->h_rgbs[j] = d_rgb[b->order[j]];
         RT_CK(cudaMemcpyAsync(b->d_rgbs, b->h_rgbs.data(), sizeof(float*) * b->n, cudaMemcpyHostToDevice, st));
         RT_CK(cudaStreamSynchronize(st));
     }

@@ -8,6 +8,7 @@
 // run are admitted as budget and streams free up and their work overlaps on
 // the device.  Completion is detected with non-blocking event queries; every
 // wait of the host is bounded.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -85,9 +86,22 @@ static size_t request_bytes(const rt_scene_desc* d)
 // Launch one batch of admitted requests on stream `si` (worker thread, lock
 // held).  Every device allocation of the flight is stream-ordered on its
 // stream, so starting and retiring flights never synchronises the device.
-static void launch_flight(rt_server* S, const std::vector<uint64_t>& tickets, int si)
+static void launch_flight(rt_server* S, const std::vector<uint64_t>& admitted, int si)
 {
     cudaStream_t st = S->streams[si];
+    // the flight's work list in the batch order: cloaked scenes first, then
+    // bare gratings, then flat mirrors, fewer samples first within a kind
+    std::vector<uint64_t> tickets = admitted;
+    auto samples = [&](uint64_t t) {
+        const rt_scene_desc& d = S->req[t].desc;
+        return (int64_t)d.height * (d.centre_line ? 1 : d.width) * d.spp;
+    };
+    std::stable_sort(tickets.begin(), tickets.end(), [&](uint64_t a, uint64_t c) {
+        const rt_scene_desc &x = S->req[a].desc, &y = S->req[c].desc;
+        if (x.cloak != y.cloak) return x.cloak > y.cloak;
+        if (x.mirror != y.mirror) return x.mirror > y.mirror;
+        return samples(a) < samples(c);
+    });
     Flight f;
     f.stream = si;
     f.done = nullptr;

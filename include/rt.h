@@ -384,7 +384,8 @@ int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, 
  * variant of rt_xcorr with the same arguments, arithmetic and results.
  * Its scratch is a fixed 16 MiB device array inside the library, held by
  * every GPU that loads the library until the process exits; images with
- * min(height, 64) * width * channels > 524288 are rejected with RT_EINVAL.
+ * min(ceil(height / 64), 64) * width * channels > 524288 are rejected with
+ * RT_EINVAL.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
  * capture.  Every call shares the one array, so calls that overlap on the GPU

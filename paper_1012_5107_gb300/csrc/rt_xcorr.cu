@@ -1,9 +1,12 @@
 // rt_xcorr.cu -- image cross-correlation C(0,0) of Eqs. 14-15 (Sec. 5).
 //
-// Pass 1 sums, per row chunk and per (column, channel), the FP64 moments
-// (sum f, sum g, sum f^2, sum f g); consecutive threads read consecutive
-// floats of a row, so the loads are coalesced.  Pass 2 reduces, one block per
-// field-of-view window, the chunks and the window's columns, and forms
+// Pass 1 sums, per row chunk (64 rows) and per (column, channel), the FP64
+// moments (sum f, sum g, sum f^2, sum f g); consecutive threads read
+// consecutive floats of a row, so the loads are coalesced.  Pass 2 reduces,
+// one block per field-of-view window, the chunks and the window's columns:
+// with 64-row chunks it reads 8 records per column of a 512-row image (it
+// read 64 with 8-row chunks, and one block per window made that the call's
+// latency).  It forms
 //   C_c = (S_fg - S_f S_g / N) / (S_ff - S_f^2 / N)
 // per channel (the numerator and denominator of Eq. 15 after the mean
 // subtraction of Eq. 14) and the same ratio over the stacked channels.
@@ -16,9 +19,14 @@ namespace grt {
 struct alignas(32) Moments { double sf, sg, sff, sfg; };
 
 constexpr int kXcorrBlock = 256;
-constexpr int kXcorrChunks = 64;
+constexpr int kXcorrRows = 64;         // rows per chunk of pass 1
+constexpr int kXcorrMaxChunks = 64;
 
-int xcorr_chunks(int H) { return H < kXcorrChunks ? H : kXcorrChunks; }
+int xcorr_chunks(int H)
+{
+    const int c = (H + kXcorrRows - 1) / kXcorrRows;
+    return c < kXcorrMaxChunks ? c : kXcorrMaxChunks;
+}
 
 __global__ void __launch_bounds__(kXcorrBlock) xcorr_columns(const float* __restrict__ f, const float* __restrict__ g,
                                                            int H, int WC, int rows_per_chunk,

@@ -68,7 +68,7 @@ extern "C" int rt_xcorr_noalloc(const float* d_f, const float* d_g, int32_t heig
     const size_t need = (size_t)xcorr_chunks(height) * (size_t)width * (size_t)channels;
     if (need > kNoallocMoments) {
         set_error("rt_xcorr_noalloc: %d x %d x %d images need %zu bytes of scratch; the fixed scratch holds %zu "
-                  "bytes (min(height, 64) * width * channels must be <= %zu)",
+                  "bytes (min(ceil(height / 64), 64) * width * channels must be <= %zu)",
                   height, width, channels, need * sizeof(NoallocMoments), kNoallocMoments * sizeof(NoallocMoments),
                   kNoallocMoments);
         return RT_EINVAL;

@@ -47,7 +47,7 @@ def test_noalloc_matches_rt_xcorr_on_consecutive_calls(rt):
 
 def test_noalloc_rejects_oversized_images(rt):
     import torch
-    f = torch.zeros((64, 4096, 3), dtype=torch.float32, device="cuda")
+    f = torch.zeros((1, 180000, 3), dtype=torch.float32, device="cuda")      # 540000 moment records
     with pytest.raises(rt.RtError) as e:
         rt.xcorr_noalloc(f, f, [50.0], 50.0)
     assert e.value.code == rt.RT_EINVAL

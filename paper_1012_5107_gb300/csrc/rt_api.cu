@@ -224,6 +224,11 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->ymirror = d->mirror != RT_MIRROR_FLAT ? s->A : 0.0;
     s->box_lo[0] = -s->E2; s->box_lo[1] = s->cd.ybot; s->box_lo[2] = -s->E2;
     s->box_hi[0] = s->E2; s->box_hi[1] = s->ytop; s->box_hi[2] = s->E2;
+    for (int a = 0; a < 3; ++a) {
+        s->cam_lo[a] = (float)(s->box_lo[a] - s->C[a]);
+        s->cam_hi[a] = (float)(s->box_hi[a] - s->C[a]);
+    }
+    s->cam_ym = (float)(s->ymirror - s->C[1]);
     s->inv_m = s->m > 0 ? 1.0 / s->m : 0.0;
     s->two_over_w = 2.0 / (double)d->width;
     s->two_over_h = 2.0 / (double)d->height;

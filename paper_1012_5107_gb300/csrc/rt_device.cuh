@@ -55,6 +55,7 @@ struct DevScene {
     AirConst<double> ad;
     double ymirror;                         // the mirror cannot be met above this height
     double box_lo[3], box_hi[3];            // cloak box
+    float cam_lo[3], cam_hi[3], cam_ym;     // box bounds and ymirror relative to the camera, FP32
     double inv_m, two_over_w, two_over_h;   // sampling constants
     double A, kA, H, E2, ytop, yrec;       // grating, cloak box (E2 = E/2), record plane
     double C[3], f[3], r[3], u[3];         // camera position and basis

@@ -754,37 +754,41 @@ __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
     }
     const double px = sc.centre_line ? 0.0 : ((double)j + ox) * sc.two_over_w - 1.0;
     const double py = 1.0 - ((double)i + oy) * sc.two_over_h;
+    const double ptx = px * sc.tx, pty = py * sc.ty;
     double d[3], n2 = 0.0;
     for (int a = 0; a < 3; ++a) {
-        d[a] = sc.f[a] + px * sc.tx * sc.r[a] + py * sc.ty * sc.u[a];
+        d[a] = sc.f[a] + ptx * sc.r[a] + pty * sc.u[a];
         n2 += d[a] * d[a];
     }
     double is = (double)rsqrtf((float)n2);
     is = is * (1.5 - 0.5 * n2 * is * is);
     for (int a = 0; a < 3; ++a) d[a] *= is;
-    double t = 0.0;
+    // How far to advance: only a distance, found in FP32 (the FP64 pipe runs
+    // at 1/64 of the FP32 rate); the point reached is then formed in FP64
+    // along the FP64 direction.  2^-10 short of the first surface, with
+    // 1e-5 relative slack for the FP32 distances.
+    float t = 0.0f;
     if (d[1] < 0.0) {
-        double inv[3];
-        for (int a = 0; a < 3; ++a) {
-            inv[a] = (d[a] != 0.0) ? (double)(1.0f / (float)d[a]) : 0.0;
-            inv[a] = inv[a] * (2.0 - d[a] * inv[a]);
-        }
-        double tf = (sc.ymirror - sc.C[1]) * inv[1];          // the mirror cannot be met earlier
+        const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+        float inv[3];
+        for (int a = 0; a < 3; ++a) inv[a] = (df[a] != 0.0f) ? Mth<float>::rcp(df[a]) : 0.0f;
+        float tf = sc.cam_ym * inv[1];                              // the mirror cannot be met earlier
         if (sc.cloak || (opt_flags<OPT>(sc) & RT_FLAG_PLATE)) {
-            double tn = -INFINITY, tx = INFINITY;
+            float tn = -INFINITY, tx = INFINITY;
             bool miss = false;
             for (int a = 0; a < 3; ++a) {
-                if (d[a] == 0.0) {
-                    if (sc.C[a] < sc.box_lo[a] || sc.C[a] > sc.box_hi[a]) miss = true;
+                if (df[a] == 0.0f) {
+                    if (sc.cam_lo[a] > 0.0f || sc.cam_hi[a] < 0.0f) miss = true;
                     continue;
                 }
-                const double t1 = (sc.box_lo[a] - sc.C[a]) * inv[a], t2 = (sc.box_hi[a] - sc.C[a]) * inv[a];
-                tn = fmax(tn, fmin(t1, t2));
-                tx = fmin(tx, fmax(t1, t2));
+                const float t1 = sc.cam_lo[a] * inv[a], t2 = sc.cam_hi[a] * inv[a];
+                tn = fmaxf(tn, fminf(t1, t2));
+                tx = fminf(tx, fmaxf(t1, t2));
             }
-            if (!miss && tn <= tx && tn > 0.0 && tn < tf) tf = tn;
+            if (!miss && tn <= tx && tn > 0.0f && tn < tf) tf = tn;
         }
-        if (tf > 0.0009765625) t = tf - 0.0009765625;
+        tf = tf * (1.0f - 1e-5f) - 0.0009765625f;
+        if (tf > 0.0f) t = tf;
     }
     const double Px = sc.C[0] + t * d[0];
     const double cxd = rint(Px);

@@ -735,7 +735,7 @@ __device__ __forceinline__ void advance(Cold<R>& C, R t)
 // the lever arm of the FP32 rounding of the direction is that short, and the
 // remaining distance is far above the box-entry threshold of the FP32 path.  Reciprocals and the norm use FP32 seeds refined by one
 // Newton step in FP64.
-template <class R, bool OPT, bool ADV32>
+template <class R, bool OPT>
 __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
 {
     const int i = (int)(C.pix / sc.wout), j = (int)(C.pix % sc.wout);
@@ -763,61 +763,32 @@ __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
     double is = (double)rsqrtf((float)n2);
     is = is * (1.5 - 0.5 * n2 * is * is);
     for (int a = 0; a < 3; ++a) d[a] *= is;
-    // How far to advance: 2^-10 short of the first surface.  The distance
-    // need not be exact, only the point reached along the FP64 direction.
-    // ADV32 (scenes read from a device table): found in FP32 from the
-    // camera-relative bounds, with 1e-5 relative slack -- the FP64 pipe runs
-    // at 1/64 of the FP32 rate, and at the end of a batched launch the
-    // air-only renders are bound by it.  Otherwise (scenes in the kernel
-    // parameters, whose FP64 pipe is idle there) in FP64.
-    double t = 0.0;
-    if constexpr (ADV32) {
-        if (d[1] < 0.0) {
-            const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
-            float inv[3];
-            for (int a = 0; a < 3; ++a) inv[a] = (df[a] != 0.0f) ? Mth<float>::rcp(df[a]) : 0.0f;
-            float tf = sc.cam_ym * inv[1];                              // the mirror cannot be met earlier
-            if (sc.cloak || (opt_flags<OPT>(sc) & RT_FLAG_PLATE)) {
-                float tn = -INFINITY, tx = INFINITY;
-                bool miss = false;
-                for (int a = 0; a < 3; ++a) {
-                    if (df[a] == 0.0f) {
-                        if (sc.cam_lo[a] > 0.0f || sc.cam_hi[a] < 0.0f) miss = true;
-                        continue;
-                    }
-                    const float t1 = sc.cam_lo[a] * inv[a], t2 = sc.cam_hi[a] * inv[a];
-                    tn = fmaxf(tn, fminf(t1, t2));
-                    tx = fminf(tx, fmaxf(t1, t2));
-                }
-                if (!miss && tn <= tx && tn > 0.0f && tn < tf) tf = tn;
-            }
-            tf = tf * (1.0f - 1e-5f) - 0.0009765625f;
-            if (tf > 0.0f) t = tf;
-        }
-    } else {
-        if (d[1] < 0.0) {
-            double inv[3];
+    // How far to advance: only a distance, found in FP32 (the FP64 pipe runs
+    // at 1/64 of the FP32 rate); the point reached is then formed in FP64
+    // along the FP64 direction.  2^-10 short of the first surface, with
+    // 1e-5 relative slack for the FP32 distances.
+    float t = 0.0f;
+    if (d[1] < 0.0) {
+        const float df[3] = {(float)d[0], (float)d[1], (float)d[2]};
+        float inv[3];
+        for (int a = 0; a < 3; ++a) inv[a] = (df[a] != 0.0f) ? Mth<float>::rcp(df[a]) : 0.0f;
+        float tf = sc.cam_ym * inv[1];                              // the mirror cannot be met earlier
+        if (sc.cloak || (opt_flags<OPT>(sc) & RT_FLAG_PLATE)) {
+            float tn = -INFINITY, tx = INFINITY;
+            bool miss = false;
             for (int a = 0; a < 3; ++a) {
-                inv[a] = (d[a] != 0.0) ? (double)(1.0f / (float)d[a]) : 0.0;
-                inv[a] = inv[a] * (2.0 - d[a] * inv[a]);
-            }
-            double tf = (sc.ymirror - sc.C[1]) * inv[1];          // the mirror cannot be met earlier
-            if (sc.cloak || (opt_flags<OPT>(sc) & RT_FLAG_PLATE)) {
-                double tn = -INFINITY, tx = INFINITY;
-                bool miss = false;
-                for (int a = 0; a < 3; ++a) {
-                    if (d[a] == 0.0) {
-                        if (sc.C[a] < sc.box_lo[a] || sc.C[a] > sc.box_hi[a]) miss = true;
-                        continue;
-                    }
-                    const double t1 = (sc.box_lo[a] - sc.C[a]) * inv[a], t2 = (sc.box_hi[a] - sc.C[a]) * inv[a];
-                    tn = fmax(tn, fmin(t1, t2));
-                    tx = fmin(tx, fmax(t1, t2));
+                if (df[a] == 0.0f) {
+                    if (sc.cam_lo[a] > 0.0f || sc.cam_hi[a] < 0.0f) miss = true;
+                    continue;
                 }
-                if (!miss && tn <= tx && tn > 0.0 && tn < tf) tf = tn;
+                const float t1 = sc.cam_lo[a] * inv[a], t2 = sc.cam_hi[a] * inv[a];
+                tn = fmaxf(tn, fminf(t1, t2));
+                tx = fminf(tx, fmaxf(t1, t2));
             }
-            if (tf > 0.0009765625) t = tf - 0.0009765625;
+            if (!miss && tn <= tx && tn > 0.0f && tn < tf) tf = tn;
         }
+        tf = tf * (1.0f - 1e-5f) - 0.0009765625f;
+        if (tf > 0.0f) t = tf;
     }
     const double Px = sc.C[0] + t * d[0];
     const double cxd = rint(Px);
@@ -1553,10 +1524,10 @@ __device__ __forceinline__ int64_t grab_work(unsigned long long* counter, unsign
     return (int64_t)(base + rank);
 }
 
-template <class R, bool OPT, bool ADV32>
+template <class R, bool OPT>
 __device__ __forceinline__ void start_sample(const DevScene& sc, Cold<R>& C, int& phase, int& surf, int& steps)
 {
-    camera_start<R, OPT, ADV32>(sc, C);
+    camera_start<R, OPT>(sc, C);
     C.bounces = 0;
     C.events = 0;
     C.w = R(1);
@@ -1754,13 +1725,13 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
                 C.pix = pix;
                 C.sample = 0;
                 C.acc[0] = C.acc[1] = C.acc[2] = 0.0f;
-                start_sample<R, false, !Src::kParamScene>(src.scene(s), C, phase, surf, steps);
+                start_sample<R, false>(src.scene(s), C, phase, surf, steps);
             }
             const DevScene& sc = src.scene(C.scene);
             if (phase == PH_AIR) air_segment<R, INTEG, false>(sc, C, b, phase, surf, steps, src.rec_of(C.scene), st);
             if (phase == PH_DONE) {
                 if (++C.sample < sc.spp) {
-                    start_sample<R, false, !Src::kParamScene>(sc, C, phase, surf, steps);
+                    start_sample<R, false>(sc, C, phase, surf, steps);
                 } else {
                     const float inv = 1.0f / (float)sc.spp;
                     float c[3];

@@ -326,7 +326,7 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                         C.pix = pix;
                         C.sample = sample;
                         C.acc[0] = C.acc[1] = C.acc[2] = 0.0f;
-                        start_sample<R, OPT, !Src::kParamScene>(src.scene(s), C, phase, surf, steps);
+                        start_sample<R, OPT>(src.scene(s), C, phase, surf, steps);
                     }
                     const DevScene& scs = src.scene(C.scene);
                     if (phase == PH_AIR) air_segment<R, INTEG, OPT>(scs, C, b, phase, surf, steps, src.rec_of(C.scene), st);

@@ -211,6 +211,10 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
         s->cd.gcap2 = (0.25 * kTwoPi * gw) * (0.25 * kTwoPi * gw);
         s->cf.gw = (float)gw; s->cf.igw = (float)(1.0 / gw); s->cf.gkh = (float)s->cd.gkh;
         s->cf.gq = (float)s->cd.gq; s->cf.gtol = 1e-12f; s->cf.gcap2 = (float)s->cd.gcap2;
+        // continuation over |dz| <= 6e-5 w_b (FP32) or 3e-9 w_b (FP64): the terms
+        // it leaves out, of second order in |dz| / w_b, stay below the precision
+        s->cf.gpred = 4e-9f;
+        s->cd.gpred = 0.0;                    // FP64 solves at every point
     }
     for (int a = 0; a < 3; ++a) {
         s->ad.fr[a] = s->fr[a]; s->ad.ur[a] = s->ur[a]; s->ad.r[a] = s->r[a]; s->ad.Pb[a] = s->Pb[a];

@@ -34,6 +34,7 @@ struct StepConst {
     // Gaussian bump (RT_MIRROR_GAUSS): width w_b, 1/w_b, k h, h/w_b, Newton
     // stop |dW|^2 <= gtol, and the largest Newton step |dW|^2 <= gcap2
     R gw, igw, gkh, gq, gtol, gcap2;
+    R gpred;     // Gaussian bump: a step continues the medium when |dz|^2 / w_b^2 <= gpred
 };
 
 // Hot counters of a lane, kept in registers.

@@ -101,9 +101,12 @@ __device__ __forceinline__ void faddeeva(R sr, R si, R& fr, R& fi)
 // evaluated (the update after it is below the stop).  F' = -2 s F + 2i/sqrt(pi)
 // and F'' = -2 F - 2 s F' follow from F.
 // ------------------------------------------------------------------------
+// Also returned: the second derivative of g, 3 z''^2 g^5 - z''' g^4 with
+// z''' = i (h/w_b^3) F''' and F''' = -4 F' - 2 s F'', in (gpr, gpi), for
+// gauss_continue.
 template <class R>
 __device__ __forceinline__ void gauss_solve(const StepConst<R>& k, R X, R y, R& wr, R& wi, R& rr, R& ri, R& Fx,
-                                            R& Fy, LaneStats& st)
+                                            R& Fy, R& gpr, R& gpi, LaneStats& st)
 {
     const R ik = R(kInvTwoPi);
     int it = 0;
@@ -139,11 +142,31 @@ __device__ __forceinline__ void gauss_solve(const StepConst<R>& k, R X, R y, R& 
             const R tr = z2r * g2r - z2i * g2i, ti = z2r * g2i + z2i * g2r;   // z'' g^2
             Fx = -n2 * tr;
             Fy = n2 * ti;
+            if constexpr (sizeof(R) == 4) {      // only the FP32 path continues (gauss_continue)
+                const R f3r = R(-4) * f1r - R(2) * (sr * f2r - si * f2i);
+                const R f3i = R(-4) * f1i - R(2) * (sr * f2i + si * f2r);
+                const R c3 = c * k.igw;
+                const R z3r = -c3 * f3i, z3i = c3 * f3r;                         // third derivative of z
+                const R t2r = tr * tr - ti * ti, t2i = R(2) * tr * ti;           // (z'' g^2)^2
+                const R g4r = g2r * g2r - g2i * g2i, g4i = R(2) * g2r * g2i;     // g^4
+                gpr = R(3) * (t2r * gr - t2i * gi) - (z3r * g4r - z3i * g4i);
+                gpi = R(3) * (t2r * gi + t2i * gr) - (z3r * g4i + z3i * g4r);
+            } else {
+                gpr = gpi = R(0);
+            }
             break;
         }
     }
     st.newton += it;
     st.evals += 1;
+}
+
+template <class R>
+__device__ __forceinline__ void gauss_solve(const StepConst<R>& k, R X, R y, R& wr, R& wi, R& rr, R& ri, R& Fx,
+                                            R& Fy, LaneStats& st)
+{
+    R gpr, gpi;
+    gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, gpr, gpi, st);
 }
 
 // Second-order continuation of W along a displacement dz = (dx, dy) from a
@@ -160,6 +183,42 @@ __device__ __forceinline__ void gauss_predict(R& wr, R& wi, R rr, R ri, R Fx, R 
     const R tr = er * dx - ei * dy, ti = er * dy + ei * dx;
     wr += R(kTwoPi) * ti;
     wi -= R(kTwoPi) * tr;
+}
+
+// The medium at a point dz = (dx, dy) from one where W, g, g'' and the force
+// are known.  A short step (|dz|^2 / w_b^2 at most gpred) is continued:
+//   W by gauss_predict;  g + g' dz + g'' dz^2 / 2;
+//   q + conj(g) g'' dz + |g'|^2 conj(dz) for q = conj(g) g', the force being
+//   (Re q, -Im q);
+// g' from the force as in gauss_predict.  What is left out is of higher order
+// in |dz| / w_b, below the working precision for such steps.  Longer steps
+// are predicted and solved.  Returns whether it solved.
+template <class R>
+__device__ __forceinline__ bool gauss_continue(const StepConst<R>& k, R X, R y, R dx, R dy, R& wr, R& wi, R& rr,
+                                               R& ri, R& Fx, R& Fy, R& gpr, R& gpi, LaneStats& st)
+{
+    // FP64 solves every point: its threshold would admit only the shortest
+    // steps, and the extra FP64 work costs more than the solves it saves
+    if (sizeof(R) == 8 || (dx * dx + dy * dy) * (k.igw * k.igw) > k.gpred) {
+        gauss_predict(wr, wi, rr, ri, Fx, Fy, dx, dy);
+        gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, gpr, gpi, st);
+        return true;
+    }
+    const R in2 = Mth<R>::rcp(rr * rr + ri * ri);
+    const R g1r = (Fx * rr + Fy * ri) * in2, g1i = (Fx * ri - Fy * rr) * in2;     // g'
+    gauss_predict(wr, wi, rr, ri, Fx, Fy, dx, dy);
+    const R hdr = gpr * dx - gpi * dy, hdi = gpr * dy + gpi * dx;                // g'' dz
+    const R m1 = g1r * g1r + g1i * g1i;
+    const R dqr = (rr * hdr + ri * hdi) + m1 * dx;                               // conj(g) g'' dz + |g'|^2 conj(dz)
+    const R dqi = (rr * hdi - ri * hdr) - m1 * dy;
+    Fx += dqr;
+    Fy -= dqi;
+    const R nr = rr + (g1r * dx - g1i * dy) + R(0.5) * (hdr * dx - hdi * dy);
+    const R ni = ri + (g1r * dy + g1i * dx) + R(0.5) * (hdr * dy + hdi * dx);
+    rr = nr;
+    ri = ni;
+    st.evals += 1;
+    return false;
 }
 
 // ------------------------------------------------------------------------

@@ -269,14 +269,16 @@ __device__ __forceinline__ void med_force(const StepConst<R>& k, Box<R>& b)
 // A stage point (X, y) reached by (dx, dy) from the previous point, whose
 // values are in (wr, wi, rr, ri) and (Fpx, Fpy): continuation and solve; the
 // force at the new point goes to (Fx, Fy).
+// (gpr, gpi): the Gaussian medium's second derivative of dw/dz at the
+// previous point in, at the new one out (zero when unknown).
 template <class R, int INTEG>
 __device__ __forceinline__ bool med_stage(const StepConst<R>& k, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri,
-                                          R Fpx, R Fpy, R& Fx, R& Fy, LaneStats& st)
+                                          R Fpx, R Fpy, R& Fx, R& Fy, R& gpr, R& gpi, LaneStats& st)
 {
     if constexpr (gauss_of(INTEG)) {
-        gauss_predict(wr, wi, rr, ri, Fpx, Fpy, dx, dy);
-        gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, st);
-        return true;
+        Fx = Fpx;
+        Fy = Fpy;
+        return gauss_continue(k, X, y, dx, dy, wr, wi, rr, ri, Fx, Fy, gpr, gpi, st);
     } else {
         const bool solved = w0_continue(k, X, y, dx, dy, wr, wi, rr, ri, st);
         ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
@@ -290,14 +292,20 @@ __device__ __forceinline__ bool med_stage(const StepConst<R>& k, R X, R y, R dx,
 // distance between the two points, O(h^2) times the change of the force);
 // a step whose stages were all continued (a very small h) solves here, so
 // that every step solves W0 at least once and continuation errors cannot
-// add up from step to step.  The Gaussian medium only predicts here and is
-// solved with its force after the step.
+// add up from step to step.  The Gaussian medium continues or solves for its
+// force as well, which it returns in (Fx, Fy); the grating's force is left to
+// the caller.
 template <class R, int INTEG>
 __device__ __forceinline__ void med_end(const StepConst<R>& k, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri,
-                                        R Fx, R Fy, bool solved, LaneStats& st)
+                                        R& Fx, R& Fy, R& gpr, R& gpi, bool solved, LaneStats& st)
 {
     if constexpr (gauss_of(INTEG)) {
-        gauss_predict(wr, wi, rr, ri, Fx, Fy, dx, dy);
+        if (solved) {
+            gauss_continue(k, X, y, dx, dy, wr, wi, rr, ri, Fx, Fy, gpr, gpi, st);
+        } else {
+            gauss_predict(wr, wi, rr, ri, Fx, Fy, dx, dy);
+            gauss_solve(k, X, y, wr, wi, rr, ri, Fx, Fy, gpr, gpi, st);
+        }
     } else if (solved) {
         w0_continue(k, X, y, dx, dy, wr, wi, rr, ri, st);
     } else {
@@ -342,16 +350,17 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     // stage 2 at r + h/2 p
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
-    R F2x, F2y;
-    bool solved = med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, F2x, F2y, st);
+    R F2x, F2y, gpr = R(0), gpi = R(0);
+    bool solved = med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, F2x, F2y, gpr, gpi,
+                                      st);
     // stage 3 at r + h/2 (p + h/2 F1), (h/2)^2 F1 away from stage 2
     const R X3 = s.X + h2 * (s.px + h2 * s.Fx), y3 = s.y + h2 * (s.py + h2 * s.Fy);
     R F3x, F3y;
-    solved |= med_stage<R, INTEG>(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, F2x, F2y, F3x, F3y, st);
+    solved |= med_stage<R, INTEG>(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, F2x, F2y, F3x, F3y, gpr, gpi, st);
     // stage 4 at r + h (p + h/2 F2)
     const R X4 = s.X + h * (s.px + h2 * F2x), y4 = s.y + h * (s.py + h2 * F2y);
     R F4x, F4y;
-    solved |= med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, F3x, F3y, F4x, F4y, st);
+    solved |= med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, F3x, F3y, F4x, F4y, gpr, gpi, st);
     // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
     const R h6 = h * R(1.0 / 6.0), hh6 = h * h6;
     const R dX = h * s.px + hh6 * (s.Fx + F2x + F3x);
@@ -365,8 +374,10 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     kahan_add(o.z, o.cz, dZ);
     kahan_add(o.px, o.cpx, dPx);
     kahan_add(o.py, o.cpy, dPy);
-    med_end<R, INTEG>(k, o.X, o.y, o.X - X4, o.y - y4, wr, wi, rr, ri, F4x, F4y, solved, st);
+    R Fex = F4x, Fey = F4y;
+    med_end<R, INTEG>(k, o.X, o.y, o.X - X4, o.y - y4, wr, wi, rr, ri, Fex, Fey, gpr, gpi, solved, st);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
+    if constexpr (gauss_of(INTEG)) { o.Fx = Fex; o.Fy = Fey; }
     wrap_cell<R, INTEG>(o);
 }
 
@@ -404,19 +415,21 @@ __device__ __forceinline__ void rk4t_step(const StepConst<R>& k, const Box<R>& s
     // stage 2 at (r + h/2 v, v + h/2 a1)
     const R v2x = s.px + h2 * a1x, v2y = s.py + h2 * a1y, v2z = s.pz + h2 * a1z;
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
-    bool solved = med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, Fx, Fy, st);
+    R gpr = R(0), gpi = R(0);
+    bool solved = med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, Fx, Fy, gpr, gpi,
+                                      st);
     R a2x, a2y, a2z;
     accel_t(k, Fx, Fy, v2x, v2y, v2z, rr, ri, a2x, a2y, a2z);
     // stage 3 at (r + h/2 v2, v + h/2 a2)
     const R v3x = s.px + h2 * a2x, v3y = s.py + h2 * a2y, v3z = s.pz + h2 * a2z;
     const R X3 = s.X + h2 * v2x, y3 = s.y + h2 * v2y;
-    solved |= med_stage<R, INTEG>(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, Fx, Fy, Fx, Fy, st);
+    solved |= med_stage<R, INTEG>(k, X3, y3, X3 - X2, y3 - y2, wr, wi, rr, ri, Fx, Fy, Fx, Fy, gpr, gpi, st);
     R a3x, a3y, a3z;
     accel_t(k, Fx, Fy, v3x, v3y, v3z, rr, ri, a3x, a3y, a3z);
     // stage 4 at (r + h v3, v + h a3)
     const R v4x = s.px + h * a3x, v4y = s.py + h * a3y, v4z = s.pz + h * a3z;
     const R X4 = s.X + h * v3x, y4 = s.y + h * v3y;
-    solved |= med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, Fx, Fy, Fx, Fy, st);
+    solved |= med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, Fx, Fy, Fx, Fy, gpr, gpi, st);
     R a4x, a4y, a4z;
     accel_t(k, Fx, Fy, v4x, v4y, v4z, rr, ri, a4x, a4y, a4z);
     // increments h/6 (k1 + 2 k2 + 2 k3 + k4) of both halves of the state
@@ -434,7 +447,7 @@ __device__ __forceinline__ void rk4t_step(const StepConst<R>& k, const Box<R>& s
     kahan_add(o.px, o.cpx, dVx);
     kahan_add(o.py, o.cpy, dVy);
     o.pz += dVz;
-    med_end<R, INTEG>(k, o.X, o.y, o.X - X4, o.y - y4, wr, wi, rr, ri, Fx, Fy, solved, st);
+    med_end<R, INTEG>(k, o.X, o.y, o.X - X4, o.y - y4, wr, wi, rr, ri, Fx, Fy, gpr, gpi, solved, st);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
     wrap_cell<R, INTEG>(o);
 }
@@ -533,6 +546,7 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
 {
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     R Xp = s.X, yp = s.y;
+    R gpr = R(0), gpi = R(0);
     const R hpx = h * s.px, hpy = h * s.py, hh = h * h;
     R Fx[7], Fy[7];
     Fx[0] = s.Fx;
@@ -568,7 +582,7 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
             Ys = o.y;
         }
         med_stage<R, INTEG>(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, Fx[j - 2], Fy[j - 2], Fx[j - 1], Fy[j - 1],
-                            st);
+                            gpr, gpi, st);
         Xp = Xs;
         yp = Ys;
     }
@@ -1471,10 +1485,9 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         hs = k.h;
         if constexpr (integ_of(INTEG) == RT_RK4T) rk4t_step<R, INTEG>(k, s, hs, o, st);
         else rk4_step<R, INTEG>(k, s, hs, o, st);
-        // the grating's W0 at the end point is continued from the fourth
-        // stage's solve inside the step; the Gaussian medium is solved here
-        if constexpr (gauss_of(INTEG)) med_eval<R, INTEG>(k, o.X, o.y, o.wr, o.wi, o.rr, o.ri, o.Fx, o.Fy, st);
-        else ray_force(o.wr, o.wi, o.rr, o.ri, k.fk, o.Fx, o.Fy);
+        // W (and the Gaussian medium's force) at the end point come from the
+        // step; the grating's force is formed here
+        if constexpr (!gauss_of(INTEG)) ray_force(o.wr, o.wi, o.rr, o.ri, k.fk, o.Fx, o.Fy);
         ++steps;
         st.steps++;
     }

@@ -147,7 +147,8 @@ template <> struct Mth<double> {
 // sin/cos pair and one reciprocal.
 // Stop: FP32 when |dW|^2 <= tol (tol = 3.6e-8 kA: the next step would move W
 // by about |dW|^2 |W|/2, below the FP32 resolution of the force); FP64 when
-// |dW|^2 <= 6e-17 |W|.  On return (wr, wi) = W and (rr, ri) = 1/(1+W): a fresh
+// |dW|^2 |1/(1+W)| <= 1e-16, so that the error left after the step, about
+// |dW|^2 |W| |1/(1+W)| / 2 by the Newton constant, is below 5e-17 |W|.  On return (wr, wi) = W and (rr, ri) = 1/(1+W): a fresh
 // reciprocal in FP32, the one of the last iterate corrected to second order
 // in the last step in FP64 (where a division costs more than the correction).
 // The result is the number of Newton steps.
@@ -176,11 +177,11 @@ __device__ __forceinline__ void newton_w0(R kA, R X, R y, R& wr, R& wi, R& rr, R
 }
 
 template <class R>
-__device__ __forceinline__ bool w0_converged(R tol, R wr, R wi, R dr, R di)
+__device__ __forceinline__ bool w0_converged(R tol, R rr, R ri, R dr, R di)
 {
     const R d2 = dr * dr + di * di;
     if constexpr (sizeof(R) == 4) return d2 <= tol;
-    else return d2 * d2 <= (Mth<R>::kRel * Mth<R>::kRel) * (wr * wr + wi * wi);
+    else return d2 * d2 * (rr * rr + ri * ri) <= R(1e-32);
 }
 
 template <class R>
@@ -191,7 +192,7 @@ __device__ __forceinline__ int w0_solve(R kA, R tol, R X, R y, R& wr, R& wi, R& 
     for (;;) {
         newton_w0(kA, X, y, wr, wi, rr, ri, dr, di);
         ++it;
-        if (w0_converged(tol, wr, wi, dr, di) || it >= Mth<R>::kMaxIt) break;
+        if (w0_converged(tol, rr, ri, dr, di) || it >= Mth<R>::kMaxIt) break;
     }
     if constexpr (sizeof(R) == 4) {
         const R ar = R(1) + wr, ai = wi;
@@ -209,6 +210,28 @@ __device__ __forceinline__ int w0_solve(R kA, R tol, R X, R y, R& wr, R& wi, R& 
 
 // First-order continuation of W along a displacement (dx, dy):
 // W' = dW/dz = i k W / (1 + W) = i k W r.
+// Third-order continuation (the guess of an FP64 solve, which then takes one
+// Newton step where the first-order guess needed two): with u = W r and
+// t = i k r dz,  W(z + dz) = W (1 + t + r t^2/2 + r t^3 (1 - 3u)/6), from
+// W' = i k u, W'' = -k^2 u r^2 and W''' = -i k^3 u r^3 (1 - 3u).
+template <class R>
+__device__ __forceinline__ void w0_predict3(R& wr, R& wi, R rr, R ri, R dx, R dy)
+{
+    const R k = R(kTwoPi);
+    const R ar = -k * dy, ai = k * dx;                               // i k dz
+    const R tr = rr * ar - ri * ai, ti = rr * ai + ri * ar;          // t
+    const R t2r = tr * tr - ti * ti, t2i = R(2) * tr * ti;
+    const R t3r = t2r * tr - t2i * ti, t3i = t2r * ti + t2i * tr;
+    const R ur = wr * rr - wi * ri, ui = wr * ri + wi * rr;          // u = W r
+    const R vr = R(1) - R(3) * ur, vi = R(-3) * ui;                  // 1 - 3u
+    const R mr = t3r * vr - t3i * vi, mi = t3r * vi + t3i * vr;      // t^3 (1 - 3u)
+    const R sr = R(0.5) * t2r + mr * R(1.0 / 6.0), si = R(0.5) * t2i + mi * R(1.0 / 6.0);
+    const R qr = tr + (rr * sr - ri * si), qi = ti + (rr * si + ri * sr);   // t + r (t^2/2 + t^3 (1 - 3u)/6)
+    const R dwr = wr * qr - wi * qi, dwi = wr * qi + wi * qr;
+    wr += dwr;
+    wi += dwi;
+}
+
 template <class R>
 __device__ __forceinline__ void w0_predict(R& wr, R& wi, R rr, R ri, R dx, R dy)
 {

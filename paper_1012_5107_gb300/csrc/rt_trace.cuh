@@ -218,8 +218,11 @@ __device__ __forceinline__ bool w0_continue(const StepConst<R>& k, R X, R y, R d
     const R n2 = rr * rr + ri * ri;
     const R dz2 = dx * dx + dy * dy;
     const R ow = wr, owi = wi;
-    if (dz2 * n2 * (n2 > R(1) ? n2 : R(1)) <= Mth<R>::kPredTol) {
-        w0_predict(wr, wi, rr, ri, dx, dy);
+    const bool cont = dz2 * n2 * (n2 > R(1) ? n2 : R(1)) <= Mth<R>::kPredTol;
+    // FP32 predicts to first order either way; FP64 guesses a solve's start
+    // to third order (w0_predict3)
+    if (sizeof(R) == 4 || cont) w0_predict(wr, wi, rr, ri, dx, dy);
+    if (cont) {
         const R ddr = wr - ow, ddi = wi - owi;            // dW
         const R tr = rr * ddr - ri * ddi, ti = rr * ddi + ri * ddr;   // r dW
         const R nrr = rr - (rr * tr - ri * ti), nri = ri - (rr * ti + ri * tr);   // r (1 - r dW)
@@ -229,7 +232,6 @@ __device__ __forceinline__ bool w0_continue(const StepConst<R>& k, R X, R y, R d
         return false;
     }
     if constexpr (sizeof(R) == 8) w0_predict3(wr, wi, rr, ri, dx, dy);
-    else w0_predict(wr, wi, rr, ri, dx, dy);
     w0_eval(k, X, y, wr, wi, rr, ri, st);
     return true;
 }

@@ -46,8 +46,12 @@ template <> struct WTab<double> {
     static __device__ __forceinline__ double a(int n) { return kWad[n]; }
 };
 
+// Out of line: the series is evaluated at every solve and in the bump's
+// parameter, and inlining each copy overflowed the instruction cache (ncu:
+// 3.3 no_instruction stall cycles per issued instruction; 12.5 -> 10.5 ms on
+// the 512 x 512 x 4 Gaussian cloak).
 template <class R>
-__device__ __forceinline__ void faddeeva_upper(R sr, R si, R& fr, R& fi)
+__device__ __noinline__ void faddeeva_upper(R sr, R si, R& fr, R& fi)
 {
     constexpr int N = WTab<R>::N;
     const R L = WTab<R>::a(N);
@@ -228,7 +232,7 @@ __device__ __forceinline__ bool gauss_continue(const StepConst<R>& k, R X, R y, 
 // Parameter u of the bump point above abscissa x: Newton's method on x(u) = x
 // with dx/du = 1 - (h/w_b) Im F'(u/w_b), guarded by bisection on [x - h, x + h].
 template <class R>
-__device__ __forceinline__ R bump_u(const StepConst<R>& k, R x)
+__device__ __noinline__ R bump_u(const StepConst<R>& k, R x)   // out of line for the same reason
 {
     R lo = x - k.A, hi = x + k.A, u = x;
     for (int it = 0; it < 60; ++it) {

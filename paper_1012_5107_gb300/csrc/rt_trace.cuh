@@ -531,6 +531,42 @@ static __constant__ double kDpCd[6] = {dp_c(2), dp_c(3), dp_c(4), dp_c(5), dp_c(
 template <class R> __device__ __forceinline__ R dp_tab_aa(int r, int c);
 template <> __device__ __forceinline__ float dp_tab_aa<float>(int r, int c) { return kDpAAf[r][c]; }
 template <> __device__ __forceinline__ double dp_tab_aa<double>(int r, int c) { return kDpAAd[r][c]; }
+// The same coefficients for the running sums of dp45_step: row r of kDpP
+// holds (A A)_{r+2, q+1} for q = 0..6 (zero past the tableau, so that rows
+// up to 10 may be read), and kDpB, kDpEA, kDpE hold b_{q+1}, (e A)_{q+1}
+// and e_{q+1}.
+__host__ __device__ constexpr double dp_aap(int r, int q) { return (r + 2 <= 7 && q + 1 <= 6) ? dp_aa(r + 2, q + 1) : 0.0; }
+#define RT_DPP_ROW(T, r) {(T)dp_aap(r, 0), (T)dp_aap(r, 1), (T)dp_aap(r, 2), (T)dp_aap(r, 3), (T)dp_aap(r, 4), \
+                          (T)dp_aap(r, 5), (T)dp_aap(r, 6)}
+#define RT_DPP_TABLE(T) {RT_DPP_ROW(T, 0), RT_DPP_ROW(T, 1), RT_DPP_ROW(T, 2), RT_DPP_ROW(T, 3), RT_DPP_ROW(T, 4), \
+                         RT_DPP_ROW(T, 5), RT_DPP_ROW(T, 6), RT_DPP_ROW(T, 7), RT_DPP_ROW(T, 8), RT_DPP_ROW(T, 9), \
+                         RT_DPP_ROW(T, 10)}
+#define RT_DPV(T, f) {(T)f(1), (T)f(2), (T)f(3), (T)f(4), (T)f(5), (T)f(6), (T)f(7)}
+__host__ __device__ constexpr double dp_b(int l) { return dp_a(7, l); }
+static __constant__ float kDpPf[11][7] = RT_DPP_TABLE(float);
+static __constant__ double kDpPd[11][7] = RT_DPP_TABLE(double);
+static __constant__ float kDpBf[7] = RT_DPV(float, dp_b);
+static __constant__ double kDpBd[7] = RT_DPV(double, dp_b);
+static __constant__ float kDpEAf[7] = RT_DPV(float, dp_ea);
+static __constant__ double kDpEAd[7] = RT_DPV(double, dp_ea);
+static __constant__ float kDpEf[7] = RT_DPV(float, dp_e);
+static __constant__ double kDpEd[7] = RT_DPV(double, dp_e);
+#undef RT_DPP_ROW
+#undef RT_DPP_TABLE
+#undef RT_DPV
+template <class R> struct DpTab;
+template <> struct DpTab<float> {
+    static __device__ __forceinline__ float p(int r, int q) { return kDpPf[r][q]; }
+    static __device__ __forceinline__ float b(int q) { return kDpBf[q]; }
+    static __device__ __forceinline__ float ea(int q) { return kDpEAf[q]; }
+    static __device__ __forceinline__ float e(int q) { return kDpEf[q]; }
+};
+template <> struct DpTab<double> {
+    static __device__ __forceinline__ double p(int r, int q) { return kDpPd[r][q]; }
+    static __device__ __forceinline__ double b(int q) { return kDpBd[q]; }
+    static __device__ __forceinline__ double ea(int q) { return kDpEAd[q]; }
+    static __device__ __forceinline__ double e(int q) { return kDpEd[q]; }
+};
 template <class R> __device__ __forceinline__ R dp_tab_c(int r);
 template <> __device__ __forceinline__ float dp_tab_c<float>(int r) { return kDpCf[r]; }
 template <> __device__ __forceinline__ double dp_tab_c<double>(int r) { return kDpCd[r]; }
@@ -545,8 +581,8 @@ template <> __device__ __forceinline__ double dp_tab_c<double>(int r) { return k
 // r + h p + h^2 sum_l (b A)_l F_l and p + h sum_j b_j F_j, and the position
 // error h^2 sum_l (e A)_l F_l -- the same method with only the forces kept.
 template <class R, int INTEG>
-__device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
-                                          LaneStats& st)
+__device__ __forceinline__ void dp45_step_table(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
+                                                LaneStats& st)
 {
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     R Xp = s.X, yp = s.y;
@@ -608,6 +644,91 @@ __device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s
     e[2] = h * gx;
     e[3] = h * gy;
     wrap_cell<R, INTEG>(o);
+}
+
+// The same step with running sums in place of the table of stage forces,
+// which the rolled stage loop indexes and so keeps in local memory.
+template <class R, int INTEG>
+__device__ __forceinline__ void dp45_step_sums(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
+                                               LaneStats& st)
+{
+    R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
+    R Xp = s.X, yp = s.y;
+    R gpr = R(0), gpi = R(0);
+    const R hpx = h * s.px, hpy = h * s.py, hh = h * h;
+    // Running sums instead of a table of the stage forces (which a rolled
+    // stage loop would keep in local memory): slot m holds the position sum
+    // sum_l (A A)_{j+m, l} F_l of stage j + m over the forces known so far;
+    // M, EA and E the momentum sum b.F and the error sums (e A).F and e.F.
+    R Sx[6], Sy[6];
+#pragma unroll
+    for (int m = 0; m < 6; ++m) Sx[m] = Sy[m] = R(0);
+    R Mx = R(0), My = R(0), EAx = R(0), EAy = R(0), Ex = R(0), Ey = R(0);
+    R Fcx = s.Fx, Fcy = s.Fy;                          // the newest force (stage j - 1)
+#pragma unroll 1
+    for (int j = 2; j <= 7; ++j) {
+        const int q = j - 2;                           // its index
+        const R b = DpTab<R>::b(q), ea = DpTab<R>::ea(q), ee = DpTab<R>::e(q);
+        Mx += b * Fcx; My += b * Fcy;
+        EAx += ea * Fcx; EAy += ea * Fcy;
+        Ex += ee * Fcx; Ey += ee * Fcy;
+#pragma unroll
+        for (int m = 0; m < 6; ++m) {
+            const R a = DpTab<R>::p(q + m, q);
+            Sx[m] += a * Fcx;
+            Sy[m] += a * Fcy;
+        }
+        R Xs, Ys;
+        if (j < 7) {
+            Xs = s.X + (dp_tab_c<R>(j - 2) * hpx + hh * Sx[0]);
+            Ys = s.y + (dp_tab_c<R>(j - 2) * hpy + hh * Sy[0]);
+        } else {
+            o = s;
+            kahan_add(o.X, o.cX, hpx + hh * Sx[0]);
+            kahan_add(o.y, o.cy, hpy + hh * Sy[0]);
+            kahan_add(o.z, o.cz, h * s.pz);
+            kahan_add(o.px, o.cpx, h * Mx);
+            kahan_add(o.py, o.cpy, h * My);
+            Xs = o.X;
+            Ys = o.y;
+        }
+        R Fnx, Fny;
+        med_stage<R, INTEG>(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, Fcx, Fcy, Fnx, Fny, gpr, gpi, st);
+        Fcx = Fnx;
+        Fcy = Fny;
+        Xp = Xs;
+        yp = Ys;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) {
+            Sx[m] = Sx[m + 1];
+            Sy[m] = Sy[m + 1];
+        }
+        Sx[5] = Sy[5] = R(0);
+    }
+    // the force at the solution (stage 7) enters the momentum error only
+    Ex += DpTab<R>::e(6) * Fcx;
+    Ey += DpTab<R>::e(6) * Fcy;
+    o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
+    o.Fx = Fcx;
+    o.Fy = Fcy;
+    e[0] = hh * EAx;
+    e[1] = hh * EAy;
+    e[2] = h * Ex;
+    e[3] = h * Ey;
+    wrap_cell<R, INTEG>(o);
+}
+
+// FP32 takes the running sums (13 % faster on the 1920 x 1080 workload);
+// FP64 the table, since the sums' 24 more registers cost it occupancy (4 %
+// slower).
+template <class R, int INTEG>
+__device__ __forceinline__ void dp45_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
+                                          LaneStats& st)
+{
+    if constexpr (sizeof(R) == 4)
+        dp45_step_sums<R, INTEG>(k, s, h, o, e, st);
+    else
+        dp45_step_table<R, INTEG>(k, s, h, o, e, st);
 }
 
 // One step of the scene's integrator of size h from s into o (for event

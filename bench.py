@@ -148,8 +148,9 @@ class Step:
         self.order = ["cloak", "cloak_line", "bare", "bare_line", "mirror", "mirror_line"]
         self.batch = rt.Batch([self.scenes[k] for k in self.order])
         self.outs = [self.img[k] for k in self.order]
-        # launches of our kernels per step: 1 batched render + 4 cross-correlation calls of 2 kernels each
-        self.launches = 1 + 4 * 2
+        # launches of our kernels per step: 1 batched render, 2 cross-correlation
+        # calls of 3 kernels (full images) and 2 of 1 kernel (centre lines)
+        self.launches = 1 + 2 * 3 + 2 * 1
 
     def run(self, ev_render=None):
         rt, st = self.rt, self.stream

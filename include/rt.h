@@ -382,8 +382,9 @@ int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, 
  * allocation call (which can synchronise the device or take a driver lock) is
  * not acceptable.  The paper has no counterpart: this is an interface
  * variant of rt_xcorr with the same arguments, arithmetic and results.
- * Its scratch is a fixed 16 MiB device array inside the library, held by
- * every GPU that loads the library until the process exits; images with
+ * Its scratch is a fixed device array of 16 MiB and 129 KiB inside the
+ * library, held by every GPU that loads the library until the process
+ * exits; images with
  * min(ceil(height / 64), 64) * width * channels > 524288 are rejected with
  * RT_EINVAL.
  * The first call on a device looks up the array's device address (once per

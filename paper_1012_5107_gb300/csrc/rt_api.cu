@@ -543,11 +543,11 @@ int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, 
     Windows win;
     fov_windows(width, hfov_deg, fov_deg, n_fov, &win);
     cudaStream_t st = (cudaStream_t)stream;
-    const size_t bytes = (size_t)xcorr_chunks(height) * width * channels * 4 * sizeof(double);
+    const size_t bytes = xcorr_scratch_bytes(height, width, channels);
     void* partial = nullptr;
-    RT_CK(cudaMallocAsync(&partial, bytes, st));
+    if (bytes) RT_CK(cudaMallocAsync(&partial, bytes, st));
     cudaError_t e = launch_xcorr(d_f, d_g, height, width, channels, win, partial, d_out, st);
-    cudaError_t e2 = cudaFreeAsync(partial, st);
+    cudaError_t e2 = bytes ? cudaFreeAsync(partial, st) : cudaSuccess;
     RT_CK(e);
     RT_CK(e2);
     return RT_OK;

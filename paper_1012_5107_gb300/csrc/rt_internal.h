@@ -63,10 +63,14 @@ cudaError_t launch_render(const DevScene& sc, int precision, int variant, int mi
 cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,
                           cudaStream_t stream);
 
-// Cross-correlation: column moments into `partial` (nchunks x W*C double4),
-// then one block per window.
+// Cross-correlation: column moments per row chunk (nchunks x W*C double4,
+// padded to 256 bytes), then window slices (kXcorrTailBytes), then C.
+// `scratch` holds xcorr_scratch_bytes(H, W, C) bytes, 256-byte aligned (none
+// for the small images that one block takes).
+constexpr size_t kXcorrTailBytes = 129 * 1024;
 int xcorr_chunks(int H);
-cudaError_t launch_xcorr(const float* f, const float* g, int H, int W, int C, const Windows& win, void* partial,
+size_t xcorr_scratch_bytes(int H, int W, int C);
+cudaError_t launch_xcorr(const float* f, const float* g, int H, int W, int C, const Windows& win, void* scratch,
                          double* out, cudaStream_t stream);
 
 // Columns of a width-W image inside each field of view (host).

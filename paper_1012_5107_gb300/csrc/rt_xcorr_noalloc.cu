@@ -6,7 +6,8 @@
 // in which an allocation call (which can synchronise the device or take a
 // driver lock) is not acceptable.  This entry point runs the same two
 // kernels as rt_xcorr but keeps their scratch -- the per-chunk column
-// moments -- in the file-scope device array below instead of allocating it.
+// moments and the window slices -- in the file-scope device array below
+// instead of allocating it.
 //
 // The array is a fixed 16 MiB that every GPU which loads the library holds
 // until the process exits.  Host code must not pass the array's name to a
@@ -24,10 +25,12 @@ struct alignas(32) NoallocMoments {
     double v[4];
 };
 
-// Largest scratch in 32-byte moment records: 16 MiB.
+// Largest column-moment scratch in 32-byte moment records: 16 MiB; the array
+// adds the window slices and the padding between the two.
 constexpr size_t kNoallocMoments = (size_t)16 << 20 >> 5;
+constexpr size_t kNoallocRecords = kNoallocMoments + (kXcorrTailBytes + 256) / sizeof(NoallocMoments);
 
-static __device__ __align__(256) NoallocMoments g_xcorr_scratch[kNoallocMoments];
+static __device__ __align__(256) NoallocMoments g_xcorr_scratch[kNoallocRecords];
 
 constexpr int kNoallocMaxDevices = 64;
 static std::mutex g_noalloc_mutex;
@@ -66,7 +69,7 @@ extern "C" int rt_xcorr_noalloc(const float* d_f, const float* d_g, int32_t heig
     for (int q = 0; q < n_fov; ++q)
         if (!(fov_deg[q] >= 0.0)) { set_error("fov_deg must be >= 0"); return RT_EINVAL; }
     const size_t need = (size_t)xcorr_chunks(height) * (size_t)width * (size_t)channels;
-    if (need > kNoallocMoments) {
+    if (need > kNoallocMoments || xcorr_scratch_bytes(height, width, channels) > sizeof(g_xcorr_scratch)) {
         set_error("rt_xcorr_noalloc: %d x %d x %d images need %zu bytes of scratch; the fixed scratch holds %zu "
                   "bytes (min(ceil(height / 64), 64) * width * channels must be <= %zu)",
                   height, width, channels, need * sizeof(NoallocMoments), kNoallocMoments * sizeof(NoallocMoments),

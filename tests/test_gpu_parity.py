@@ -318,7 +318,9 @@ def test_texture_background(rt, torch, orc):
 # ---------------------------------------------------------------------------
 def test_xcorr_parity(rt, torch, orc):
     rng = np.random.default_rng(2)
-    for H, W in [(64, 64), (37, 129), (512, 1), (300, 512)]:
+    # (512, 1), (20, 10), (7, 21), (65, 21): one block; (66, 21) is the
+    # first height past its 4096 values; the rest take the three passes
+    for H, W in [(64, 64), (37, 129), (512, 1), (300, 512), (20, 10), (7, 21), (65, 21), (66, 21)]:
         f = rng.random((H, W, 3)).astype(np.float32)
         g = (0.6 * f + 0.4 * rng.random((H, W, 3))).astype(np.float32)
         fovs = [0.0, 10.0, 25.0, 50.0]

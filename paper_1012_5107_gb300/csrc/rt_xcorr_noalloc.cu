@@ -4,12 +4,12 @@
 // Some callers cannot allocate: hosts that hand all device memory to their
 // own pool and forbid allocations behind its back, and latency-bound loops
 // in which an allocation call (which can synchronise the device or take a
-// driver lock) is not acceptable.  This entry point runs the same two
+// driver lock) is not acceptable.  This entry point runs the same
 // kernels as rt_xcorr but keeps their scratch -- the per-chunk column
 // moments and the window slices -- in the file-scope device array below
 // instead of allocating it.
 //
-// The array is a fixed 16 MiB that every GPU which loads the library holds
+// The array is a fixed 16 MiB (and the slices' 129 KiB) that every GPU which loads the library holds
 // until the process exits.  Host code must not pass the array's name to a
 // kernel: in host code it names a host-side stand-in, not device memory.  The
 // device address is taken with cudaGetSymbolAddress, once per device, with
@@ -94,8 +94,8 @@ extern "C" int rt_xcorr_noalloc(const float* d_f, const float* d_g, int32_t heig
     }
     Windows win;
     fov_windows(width, hfov_deg, fov_deg, n_fov, &win);
-    // the first kernel overwrites every scratch record the second one reads,
-    // so nothing has to be cleared between calls
+    // each kernel reads only scratch records that an earlier kernel of the
+    // same call wrote, so nothing has to be cleared between calls
     e = launch_xcorr(d_f, d_g, height, width, channels, win, scratch, d_out, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         set_error("rt_xcorr_noalloc: %s", cudaGetErrorString(e));

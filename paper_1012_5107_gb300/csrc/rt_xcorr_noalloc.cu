@@ -9,8 +9,8 @@
 // moments and the window slices -- in the file-scope device array below
 // instead of allocating it.
 //
-// The array is a fixed 16 MiB (and the slices' 129 KiB) that every GPU which loads the library holds
-// until the process exits.  Host code must not pass the array's name to a
+// The array is a fixed 16 MiB (and the slices' 129 KiB) that every GPU
+// which loads the library holds until the process exits.  Host code must not pass the array's name to a
 // kernel: in host code it names a host-side stand-in, not device memory.  The
 // device address is taken with cudaGetSymbolAddress, once per device, with
 // that device current, by the first call of rt_xcorr_noalloc on the device.

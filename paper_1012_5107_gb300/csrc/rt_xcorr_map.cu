@@ -1,9 +1,10 @@
 // rt_xcorr_map.cu -- the cross-correlation function C(di, dj) of Eq. 15 over
 // pixel shifts, its peak and its mean over several reference pairs (Sec. 5).
 //
-// Pass 1 (one block per pair and channel) forms, over the field-of-view window
-// of columns j0..j1-1, the means of Eq. 14 and the denominator
-// sum (f - <f>)^2 of Eq. 15 in FP64.
+// Pass 1 forms, over the field-of-view window of columns j0..j1-1, the means
+// of Eq. 14 and the denominator sum (f - <f>)^2 of Eq. 15 in FP64: blocks of
+// 4 image rows per pair sum them (FP64 is slow on this GPU, so the work is
+// spread over many SMs), then a block per pair and channel adds the chunks.
 // Pass 2 is a direct correlation in tiles: a block owns 8 x 32 R shifts
 // (di, dj) and a chunk of 32 image rows of one pair and channel; per row it
 // stages the window's f row and the 8 g rows the shifts need (zero outside
@@ -13,6 +14,7 @@
 // Pass 3 sums the chunks in FP64, divides by the denominators, stacks the
 // channels (sum of numerators over sum of denominators) and averages the maps
 // of the pairs; pass 4 finds the peak of the stacked mean map and its shift.
+#include <algorithm>
 #include <cmath>
 #include <vector>
 
@@ -33,25 +35,63 @@ struct MapImages {
     const float* g[kMapMaxPairs];
 };
 
-__global__ void __launch_bounds__(256) xmap_moments(MapImages im, int H, int W, int C, int j0, int j1,
-                                                    double* __restrict__ stats)
+constexpr int kMomRows = 4;       // image rows per block of pass 1
+constexpr int kMomBlock = 256;
+
+// A window row's values, (i W + j0) C ... (i W + j1) C, are contiguous, and
+// the stride T is a multiple of C, so thread t meets only channel t mod C;
+// the block's per-channel sums go to part[((pair nchunks + chunk) C + c) 3 + q]
+// (q: sum f, sum g, sum f^2).
+__global__ void __launch_bounds__(kMomBlock) xmap_moment_rows(MapImages im, int H, int W, int C, int j0, int j1,
+                                                              int nchunks, double* __restrict__ part)
 {
-    const int pair = blockIdx.x / C, c = blockIdx.x % C;
+    __shared__ double red[3][kMomBlock];
+    const int chunk = blockIdx.x, pair = blockIdx.y;
     const float* f = im.f[pair];
     const float* g = im.g[pair];
-    const int wc = j1 - j0;
-    const int64_t n = (int64_t)H * wc;
+    const int T = (kMomBlock / C) * C;
+    const int len = (j1 - j0) * C;
+    const int t = threadIdx.x;
+    const int i0 = chunk * kMomRows, i1 = min(H, i0 + kMomRows);
     double sf = 0.0, sg = 0.0, sff = 0.0;
-    for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-        const int i = (int)(t / wc), j = j0 + (int)(t % wc);
-        const double a = __ldg(f + ((int64_t)i * W + j) * C + c), b = __ldg(g + ((int64_t)i * W + j) * C + c);
-        sf += a;
-        sg += b;
-        sff += a * a;
+    if (t < T) {
+        for (int i = i0; i < i1; ++i) {
+            const int64_t base = ((int64_t)i * W + j0) * C;
+#pragma unroll 4
+            for (int e = t; e < len; e += T) {
+                const double a = __ldg(f + base + e), b = __ldg(g + base + e);
+                sf += a;
+                sg += b;
+                sff += a * a;
+            }
+        }
     }
-    __shared__ double red[3][8];
+    red[0][t] = sf;
+    red[1][t] = sg;
+    red[2][t] = sff;
+    __syncthreads();
+    if (t < 3 * C) {
+        const int q = t / C, c = t - q * C;
+        double acc = 0.0;
+        for (int k = c; k < T; k += C) acc += red[q][k];
+        part[(((int64_t)pair * nchunks + chunk) * C + c) * 3 + q] = acc;
+    }
+}
+
+// Block per (pair, channel): the chunks' sums, then the statistics.
+__global__ void __launch_bounds__(128) xmap_moment_stats(const double* __restrict__ part, int H, int C, int j0,
+                                                         int j1, int nchunks, double* __restrict__ stats)
+{
+    const int pc = blockIdx.x, pair = pc / C, c = pc % C;
+    double v[3] = {0.0, 0.0, 0.0};
+    for (int k = threadIdx.x; k < nchunks; k += blockDim.x) {
+        const double* p = part + (((int64_t)pair * nchunks + k) * C + c) * 3;
+        v[0] += p[0];
+        v[1] += p[1];
+        v[2] += p[2];
+    }
+    __shared__ double red[3][4];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    double v[3] = {sf, sg, sff};
     for (int q = 0; q < 3; ++q) {
         double x = v[q];
         for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
@@ -59,14 +99,13 @@ __global__ void __launch_bounds__(256) xmap_moments(MapImages im, int H, int W, 
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        double t[3] = {0.0, 0.0, 0.0};
-        for (int q = 0; q < 3; ++q)
-            for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t[q] += red[q][w];
-        const double N = (double)n;
+        double t[3];
+        for (int q = 0; q < 3; ++q) t[q] = red[q][0] + red[q][1] + red[q][2] + red[q][3];
+        const double N = (double)H * (double)(j1 - j0);
         const double mf = t[0] / N, mg = t[1] / N;          // Eq. 14
-        stats[3 * blockIdx.x + 0] = mf;
-        stats[3 * blockIdx.x + 1] = mg;
-        stats[3 * blockIdx.x + 2] = t[2] - t[0] * mf;       // sum (f - <f>)^2, Eq. 15 denominator
+        stats[3 * pc + 0] = mf;
+        stats[3 * pc + 1] = mg;
+        stats[3 * pc + 2] = t[2] - t[0] * mf;               // sum (f - <f>)^2, Eq. 15 denominator
     }
 }
 
@@ -224,13 +263,21 @@ extern "C" int rt_xcorr_map(const float* const* d_f, const float* const* d_g, in
     const int nchunks = (height + kMapRows - 1) / kMapRows;
     const int npc = n_pairs * channels;
     cudaStream_t st = (cudaStream_t)stream;
+    const int mchunks = (height + kMomRows - 1) / kMomRows;
     double* stats = nullptr;
     double* partial = nullptr;
+    // the moment sums of pass 1 share the buffer of pass 2's partial sums,
+    // which they precede; the buffer holds the larger of the two
+    const size_t part_doubles = std::max((size_t)npc * nchunks * nshift, (size_t)n_pairs * mchunks * channels * 3);
     cudaError_t e = cudaMallocAsync((void**)&stats, sizeof(double) * 3 * npc, st);
-    if (e == cudaSuccess)
-        e = cudaMallocAsync((void**)&partial, sizeof(double) * (size_t)npc * nchunks * nshift, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&partial, sizeof(double) * part_doubles, st);
     if (e == cudaSuccess) {
-        xmap_moments<<<npc, 256, 0, st>>>(im, height, width, channels, j0, j1, stats);
+        xmap_moment_rows<<<dim3(mchunks, n_pairs), kMomBlock, 0, st>>>(im, height, width, channels, j0, j1, mchunks,
+                                                                        partial);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        xmap_moment_stats<<<npc, 128, 0, st>>>(partial, height, channels, j0, j1, mchunks, stats);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

@@ -5,15 +5,19 @@
 // of Eq. 14 and the denominator sum (f - <f>)^2 of Eq. 15 in FP64: blocks of
 // 4 image rows per pair sum them (FP64 is slow on this GPU, so the work is
 // spread over many SMs), then a block per pair and channel adds the chunks.
-// Pass 2 is a direct correlation in tiles: a block owns 8 x 32 R shifts
-// (di, dj) and a chunk of 32 image rows of one pair and channel; per row it
-// stages the window's f row and the 8 g rows the shifts need (zero outside
-// the window, where the finite photographs have no values) in shared memory,
-// and every thread accumulates its R shifts' products over the chunk with
-// FP32 FMA (see xmap_tiles).
-// Pass 3 sums the chunks in FP64, divides by the denominators, stacks the
-// channels (sum of numerators over sum of denominators) and averages the maps
-// of the pairs; pass 4 finds the peak of the stacked mean map and its shift.
+// Pass 2 is a direct correlation in tiles: a block owns 16 R x 16 R shifts
+// (di, dj) and a chunk of 8 image rows x 128 columns of one pair and
+// channel; it stages the chunk of f and the window of g its shifts need (zero
+// outside the field-of-view window, where the finite photographs have no
+// values) in shared memory, and each thread accumulates the products of its
+// R x R shifts over the chunk with FP32 FMA (see xmap_tiles).
+// Pass 3 adds, per shift, pair, channel and column chunk, the row chunks'
+// sums with compensated (Kahan) FP32 summation, whose error is of the order
+// of one FP32 rounding of the result, below the rounding already in each
+// chunk's sum (FP64 adds are 64 times slower on this GPU).  Pass 4 adds the
+// column chunks in FP64, divides by the denominators, stacks the channels
+// (sum of numerators over sum of denominators) and averages the maps of the
+// pairs; pass 5 finds the peak of the stacked mean map and its shift.
 #include <algorithm>
 #include <cmath>
 #include <vector>
@@ -22,12 +26,21 @@
 
 namespace grt {
 
-constexpr int kMapTDI = 8;        // shifts in di per block
-constexpr int kMapTDJ = 32;       // shifts in dj per block (one warp)
-constexpr int kMapTW = 128;       // columns staged per step
-constexpr int kMapRows = 32;      // image rows per chunk
-constexpr int kMapBlock = kMapTDI * kMapTDJ;
+constexpr int kMapT = 16;         // threads along di and along dj
+constexpr int kMapRows = 8;       // image rows per chunk
+constexpr int kMapCols = 128;     // image columns per chunk
+constexpr int kMapBlock = kMapT * kMapT;
 constexpr int kMapMaxShift = 64;
+
+// Staged g window of a block with R x R shifts per thread: rows x padded
+// columns (one column past the window is read, never used, by the sliding
+// loads of the last column).
+template <int R> struct MapTile {
+    static constexpr int TD = kMapT * R;                  // shifts per block along di and dj
+    static constexpr int GR = kMapRows + TD - 1;
+    static constexpr int GC = kMapCols + TD;
+    static constexpr size_t smem = sizeof(float) * ((size_t)GR * GC + (size_t)kMapRows * kMapCols);
+};
 constexpr int kMapMaxPairs = 64;
 
 struct MapImages {
@@ -109,78 +122,111 @@ __global__ void __launch_bounds__(128) xmap_moment_stats(const double* __restric
     }
 }
 
-// One block: 8 row shifts (one per warp) x 32 R column shifts, lane l owning
-// the R consecutive column shifts dj_lo + l R + k.  Along a staged row a lane
-// keeps the R g values its shifts need in registers and slides them by one
-// per column, so each step costs one broadcast f load and one g load for R
-// FMAs; R is odd, so the lanes' g loads (stride R) hit distinct banks.
+// Thread (ty, tx) owns the shifts di = di_lo + ty R + a, dj = dj_lo + tx R + b
+// (a, b < R).  The product f(i, j) g(i + di, j + dj) of chunk row r and column
+// q reads g_s[r + ty R + a][q + tx R + b]; along q each of the R g rows a
+// thread reads slides by one column, so a column costs one broadcast f load
+// and R g loads for R^2 FMAs.  The chunk's sum per shift is FP32 (8 x 128
+// products); part[((pc nchunks + chunk) nshift + s)], chunk = rc ncc + cc.
 template <int R>
 __global__ void __launch_bounds__(kMapBlock) xmap_tiles(MapImages im, const double* __restrict__ stats, int H, int W,
-                                                        int C, int j0, int j1, int max_di, int max_dj, int nchunks,
-                                                        double* __restrict__ partial)
+                                                        int C, int j0, int j1, int max_di, int max_dj, int ncc,
+                                                        int nchunks, float* __restrict__ part)
 {
-    constexpr int TJ = kMapTDJ * R;              // column shifts per block
-    constexpr int GW = kMapTW + TJ;              // staged g columns per row
-    __shared__ float f_s[kMapTW];
-    __shared__ float g_s[kMapTDI][GW];
+    using Tl = MapTile<R>;
+    extern __shared__ float map_smem[];
+    float* g_s = map_smem;                                   // [GR][GC]
+    float* f_s = map_smem + (size_t)Tl::GR * Tl::GC;         // [kMapRows][kMapCols]
     const int ndi = 2 * max_di + 1, ndj = 2 * max_dj + 1;
-    const int tiles_dj = (ndj + TJ - 1) / TJ;
+    const int tiles_dj = (ndj + Tl::TD - 1) / Tl::TD;
     const int tdi = blockIdx.x / tiles_dj, tdj = blockIdx.x % tiles_dj;
     const int chunk = blockIdx.y;
+    const int rc = chunk / ncc, cc = chunk % ncc;
     const int pc = blockIdx.z;
     const int pair = pc / C, c = pc % C;
     const float* f = im.f[pair];
     const float* g = im.g[pair];
     const float mf = (float)stats[3 * pc + 0], mg = (float)stats[3 * pc + 1];
-    const int di_lo = -max_di + tdi * kMapTDI, dj_lo = -max_dj + tdj * TJ;
-    const int ty = threadIdx.x / kMapTDJ, tx = threadIdx.x % kMapTDJ;
-    const int i0 = chunk * kMapRows, i1 = min(H, i0 + kMapRows);
-    float acc[R];
+    const int di_lo = -max_di + tdi * Tl::TD, dj_lo = -max_dj + tdj * Tl::TD;
+    const int i0 = rc * kMapRows, jc = j0 + cc * kMapCols;
+    for (int k = threadIdx.x; k < kMapRows * kMapCols; k += kMapBlock) {
+        const int r = k / kMapCols, q = k % kMapCols;
+        const int i = i0 + r, j = jc + q;
+        f_s[k] = (i < H && j < j1) ? __ldg(f + ((int64_t)i * W + j) * C + c) - mf : 0.0f;
+    }
+    for (int k = threadIdx.x; k < Tl::GR * Tl::GC; k += kMapBlock) {
+        const int r = k / Tl::GC, q = k % Tl::GC;
+        const int i = i0 + di_lo + r, j = jc + dj_lo + q;
+        g_s[k] = (i >= 0 && i < H && j >= j0 && j < j1) ? __ldg(g + ((int64_t)i * W + j) * C + c) - mg : 0.0f;
+    }
+    __syncthreads();
+    const int ty = threadIdx.x / kMapT, tx = threadIdx.x % kMapT;
+    float acc[R][R];
 #pragma unroll
-    for (int k = 0; k < R; ++k) acc[k] = 0.0f;
-    const float* gr = &g_s[ty][tx * R];
-    for (int i = i0; i < i1; ++i) {
-        for (int jt = j0; jt < j1; jt += kMapTW) {
-            for (int q = threadIdx.x; q < kMapTW; q += kMapBlock) {
-                const int j = jt + q;
-                f_s[q] = (j < j1) ? __ldg(f + ((int64_t)i * W + j) * C + c) - mf : 0.0f;
+    for (int a = 0; a < R; ++a)
+#pragma unroll
+        for (int b = 0; b < R; ++b) acc[a][b] = 0.0f;
+    for (int r = 0; r < kMapRows; ++r) {
+        const float* fr = f_s + r * kMapCols;
+        const float* gr = g_s + (size_t)(r + ty * R) * Tl::GC + tx * R;
+        float win[R][R];
+#pragma unroll
+        for (int a = 0; a < R; ++a)
+#pragma unroll
+            for (int b = 0; b < R; ++b) win[a][b] = gr[a * Tl::GC + b];
+#pragma unroll 16
+        for (int q = 0; q < kMapCols; ++q) {
+            const float fv = fr[q];
+#pragma unroll
+            for (int a = 0; a < R; ++a) {
+#pragma unroll
+                for (int b = 0; b < R; ++b) acc[a][b] = fmaf(fv, win[a][b], acc[a][b]);
+#pragma unroll
+                for (int b = 0; b + 1 < R; ++b) win[a][b] = win[a][b + 1];
+                win[a][R - 1] = gr[a * Tl::GC + q + R];
             }
-            for (int q = threadIdx.x; q < kMapTDI * GW; q += kMapBlock) {
-                const int r = q / GW, col = q % GW;
-                const int ig = i + di_lo + r, jg = jt + dj_lo + col;
-                g_s[r][col] = (ig >= 0 && ig < H && jg >= j0 && jg < j1)
-                                  ? __ldg(g + ((int64_t)ig * W + jg) * C + c) - mg
-                                  : 0.0f;
-            }
-            __syncthreads();
-            float win[R];
-#pragma unroll
-            for (int k = 0; k < R; ++k) win[k] = gr[k];
-#pragma unroll 32
-            for (int q = 0; q < kMapTW; ++q) {
-                const float fv = f_s[q];
-#pragma unroll
-                for (int k = 0; k < R; ++k) acc[k] = fmaf(fv, win[k], acc[k]);
-#pragma unroll
-                for (int k = 0; k + 1 < R; ++k) win[k] = win[k + 1];
-                win[R - 1] = gr[q + R];
-            }
-            __syncthreads();
         }
     }
-    const int di = di_lo + ty;
+    const int64_t nshift = (int64_t)ndi * ndj;
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        const int dj = dj_lo + tx * R + k;
-        if (di <= max_di && dj <= max_dj) {
-            const int s = (di + max_di) * ndj + (dj + max_dj);
-            partial[((int64_t)pc * nchunks + chunk) * ((int64_t)ndi * ndj) + s] = (double)acc[k];
+    for (int a = 0; a < R; ++a) {
+        const int di = di_lo + ty * R + a;
+#pragma unroll
+        for (int b = 0; b < R; ++b) {
+            const int dj = dj_lo + tx * R + b;
+            if (di <= max_di && dj <= max_dj) {
+                const int64_t sh = (int64_t)(di + max_di) * ndj + (dj + max_dj);
+                part[((int64_t)pc * nchunks + chunk) * nshift + sh] = acc[a][b];
+            }
         }
     }
 }
 
-__global__ void __launch_bounds__(256) xmap_finish(const double* __restrict__ partial,
-                                                   const double* __restrict__ stats, int n_pairs, int C, int nchunks,
+// Thread per (pair and channel pc, column chunk cc, shift s): the row chunks'
+// sums, compensated; colsum[(pc ncc + cc) nshift + s] = sum - compensation.
+__global__ void __launch_bounds__(256) xmap_sum(const float* __restrict__ part, int nrc, int ncc, int64_t n,
+                                                int nshift, double* __restrict__ colsum)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const int s = (int)(t % nshift);
+    const int64_t pq = t / nshift;
+    const int64_t pc = pq / ncc, cc = pq % ncc;
+    const float* p = part + ((pc * nrc * ncc) + cc) * nshift + s;
+    const int64_t stride = (int64_t)ncc * nshift;
+    float sum = 0.0f, comp = 0.0f;
+#pragma unroll 8
+    for (int k = 0; k < nrc; ++k) {
+        const float y = p[k * stride] - comp;
+        const float u = sum + y;
+        comp = (u - sum) - y;
+        sum = u;
+    }
+    colsum[t] = (double)sum - (double)comp;
+}
+
+__global__ void __launch_bounds__(256) xmap_finish(const double* __restrict__ colsum,
+                                                   const double* __restrict__ stats, int n_pairs, int C, int ncc,
                                                    int nshift, double* __restrict__ out)
 {
     const int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -191,7 +237,7 @@ __global__ void __launch_bounds__(256) xmap_finish(const double* __restrict__ pa
         for (int c = 0; c < C; ++c) {
             const int pc = p * C + c;
             double num = 0.0;
-            for (int k = 0; k < nchunks; ++k) num += partial[((int64_t)pc * nchunks + k) * nshift + s];
+            for (int q = 0; q < ncc; ++q) num += colsum[((int64_t)pc * ncc + q) * nshift + s];
             const double den = stats[3 * pc + 2];
             mean[c] += num / den;
             num_all += num;
@@ -233,6 +279,17 @@ __global__ void __launch_bounds__(1024) xmap_peak(const double* __restrict__ map
     }
 }
 
+template <int R>
+static cudaError_t launch_tiles(dim3 grid, cudaStream_t st, const MapImages& im, const double* stats, int H, int W,
+                               int C, int j0, int j1, int max_di, int max_dj, int ncc, int nchunks, float* part)
+{
+    const size_t smem = MapTile<R>::smem;
+    cudaError_t e = cudaFuncSetAttribute(xmap_tiles<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    xmap_tiles<R><<<grid, kMapBlock, smem, st>>>(im, stats, H, W, C, j0, j1, max_di, max_dj, ncc, nchunks, part);
+    return cudaGetLastError();
+}
+
 }  // namespace grt
 
 using namespace grt;
@@ -260,17 +317,28 @@ extern "C" int rt_xcorr_map(const float* const* d_f, const float* const* d_g, in
     MapImages im;
     for (int p = 0; p < n_pairs; ++p) { im.f[p] = d_f[p]; im.g[p] = d_g[p]; }
     const int ndi = 2 * max_di + 1, ndj = 2 * max_dj + 1, nshift = ndi * ndj;
-    const int nchunks = (height + kMapRows - 1) / kMapRows;
+    const int nrc = (height + kMapRows - 1) / kMapRows;
+    const int ncc = (j1 - j0 + kMapCols - 1) / kMapCols;
+    if ((int64_t)nrc * ncc > 65535) {
+        set_error("rt_xcorr_map: %d x %d window chunks of %d x %d pixels exceed 65535", nrc, ncc, kMapRows, kMapCols);
+        return RT_EINVAL;
+    }
+    const int nchunks = nrc * ncc;
     const int npc = n_pairs * channels;
     cudaStream_t st = (cudaStream_t)stream;
     const int mchunks = (height + kMomRows - 1) / kMomRows;
     double* stats = nullptr;
     double* partial = nullptr;
-    // the moment sums of pass 1 share the buffer of pass 2's partial sums,
-    // which they precede; the buffer holds the larger of the two
-    const size_t part_doubles = std::max((size_t)npc * nchunks * nshift, (size_t)n_pairs * mchunks * channels * 3);
+    // the moment sums of pass 1 (double) share the buffer of pass 2's chunk
+    // sums (float), which they precede; the buffer holds the larger of the
+    // two, then pass 3's column-chunk sums (double)
+    const size_t chunk_bytes = (std::max(sizeof(float) * (size_t)npc * nchunks * nshift,
+                                         sizeof(double) * (size_t)n_pairs * mchunks * channels * 3) + 255) &
+                               ~(size_t)255;
+    const size_t ncol = (size_t)npc * ncc * nshift;
+    const size_t part_bytes = chunk_bytes + sizeof(double) * ncol;
     cudaError_t e = cudaMallocAsync((void**)&stats, sizeof(double) * 3 * npc, st);
-    if (e == cudaSuccess) e = cudaMallocAsync((void**)&partial, sizeof(double) * part_doubles, st);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&partial, part_bytes, st);
     if (e == cudaSuccess) {
         xmap_moment_rows<<<dim3(mchunks, n_pairs), kMomBlock, 0, st>>>(im, height, width, channels, j0, j1, mchunks,
                                                                         partial);
@@ -281,22 +349,32 @@ extern "C" int rt_xcorr_map(const float* const* d_f, const float* const* d_g, in
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        // column shifts per lane: the smallest odd R with 32 R >= ndj (1, 3 or 5)
-        const int R = ndj <= kMapTDJ ? 1 : (ndj <= 3 * kMapTDJ ? 3 : 5);
-        const dim3 grid(((ndi + kMapTDI - 1) / kMapTDI) * ((ndj + kMapTDJ * R - 1) / (kMapTDJ * R)), nchunks, npc);
+        // shifts per thread along each axis: the smallest odd R with
+        // 16 R >= the larger shift range (1, 3 or 5; ranges past 80 take
+        // more tiles of R = 5)
+        const int nd = std::max(ndi, ndj);
+        const int R = nd <= kMapT ? 1 : (nd <= 3 * kMapT ? 3 : 5);
+        const int TD = kMapT * R;
+        const dim3 grid(((ndi + TD - 1) / TD) * ((ndj + TD - 1) / TD), nchunks, npc);
+        float* part = (float*)partial;
         if (R == 1)
-            xmap_tiles<1><<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj,
-                                                      nchunks, partial);
+            e = launch_tiles<1>(grid, st, im, stats, height, width, channels, j0, j1, max_di, max_dj, ncc, nchunks,
+                                part);
         else if (R == 3)
-            xmap_tiles<3><<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj,
-                                                      nchunks, partial);
+            e = launch_tiles<3>(grid, st, im, stats, height, width, channels, j0, j1, max_di, max_dj, ncc, nchunks,
+                                part);
         else
-            xmap_tiles<5><<<grid, kMapBlock, 0, st>>>(im, stats, height, width, channels, j0, j1, max_di, max_dj,
-                                                      nchunks, partial);
+            e = launch_tiles<5>(grid, st, im, stats, height, width, channels, j0, j1, max_di, max_dj, ncc, nchunks,
+                                part);
+    }
+    double* colsum = partial ? (double*)((char*)partial + chunk_bytes) : nullptr;
+    if (e == cudaSuccess) {
+        xmap_sum<<<(unsigned)((ncol + 255) / 256), 256, 0, st>>>((const float*)partial, nrc, ncc, (int64_t)ncol,
+                                                                  nshift, colsum);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        xmap_finish<<<(nshift + 255) / 256, 256, 0, st>>>(partial, stats, n_pairs, channels, nchunks, nshift, d_map);
+        xmap_finish<<<(nshift + 255) / 256, 256, 0, st>>>(colsum, stats, n_pairs, channels, ncc, nshift, d_map);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess && d_peak) {

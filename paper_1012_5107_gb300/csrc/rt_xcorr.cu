@@ -3,7 +3,8 @@
 // The window sums are FP64 moments (sum f, sum g, sum f^2, sum f g) per
 // channel, and FP64 arithmetic is slow on this GPU (two fused multiply-adds
 // per SM and cycle), so every pass spreads its FP64 work over many SMs:
-//   1. column moments per row chunk (64 rows): a block takes 32 columns of
+//   1. column moments per row chunk (64 rows; at most 64 chunks, so taller
+//      images have longer chunks): a block takes 32 columns of
 //      the flattened row (one per lane, so loads are coalesced) and splits
 //      the chunk's rows over its 8 warps, then adds the warps' sums;
 //   2. window slices: a block per (window, slice) adds the chunks' moments

@@ -137,6 +137,27 @@ template <> struct Mth<double> {
 };
 
 // ------------------------------------------------------------------------
+// Packed FP32 pairs: sm_100 and later issue two FP32 fused multiply-adds,
+// adds or multiplies of a thread in one instruction (FFMA2, FADD2, FMUL2).
+// The FP32 path keeps (x, y) components and real and imaginary parts as such
+// pairs where its arithmetic pairs up; per component every result is the
+// scalar operation's in round-to-nearest (a - b is taken as fma(b, -1, a),
+// which is exact before its one rounding).
+__device__ __forceinline__ float2 p2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 p2s(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+// compensated (Kahan) sum of both components
+__device__ __forceinline__ void kahan2(float2& sum, float2& comp, float2 inc)
+{
+    const float2 yv = sub2(inc, comp);
+    const float2 t = add2(sum, yv);
+    comp = sub2(sub2(t, sum), yv);
+    sum = t;
+}
+
 // Lambert W0 of zeta = -kA exp(i k z) (Eq. 1 with c = iA, Eq. 13).
 //
 // W e^W = zeta is solved in the equivalent form

@@ -350,6 +350,50 @@ __device__ __forceinline__ void kahan_add(R& s, R& c, R inc)
 template <class R, int INTEG>
 __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, LaneStats& st)
 {
+    if constexpr (sizeof(R) == 4) {
+        // the same step with the (x, y) arithmetic in packed pairs
+        const float h2 = 0.5f * h;
+        float wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
+        const float2 P = p2(s.X, s.y), M = p2(s.px, s.py), F1 = p2(s.Fx, s.Fy);
+        const float2 H2 = p2s(h2), H = p2s(h);
+        // stage 2 at r + h/2 p
+        const float2 D2 = mul2(H2, M);
+        const float2 P2 = fma2(H2, M, P);
+        float F2x, F2y, gpr = 0.0f, gpi = 0.0f;
+        bool solved = med_stage<R, INTEG>(k, P2.x, P2.y, D2.x, D2.y, wr, wi, rr, ri, s.Fx, s.Fy, F2x, F2y, gpr,
+                                          gpi, st);
+        // stage 3 at r + h/2 (p + h/2 F1)
+        const float2 P3 = fma2(H2, fma2(H2, F1, M), P);
+        const float2 D3 = sub2(P3, P2);
+        float F3x, F3y;
+        solved |= med_stage<R, INTEG>(k, P3.x, P3.y, D3.x, D3.y, wr, wi, rr, ri, F2x, F2y, F3x, F3y, gpr, gpi, st);
+        // stage 4 at r + h (p + h/2 F2)
+        const float2 Fs2 = p2(F2x, F2y);
+        const float2 P4 = fma2(H, fma2(H2, Fs2, M), P);
+        const float2 D4 = sub2(P4, P3);
+        float F4x, F4y;
+        solved |= med_stage<R, INTEG>(k, P4.x, P4.y, D4.x, D4.y, wr, wi, rr, ri, F3x, F3y, F4x, F4y, gpr, gpi, st);
+        // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
+        const float h6 = h * (1.0f / 6.0f), hh6 = h * h6;
+        const float2 Fs3 = p2(F3x, F3y), Fs4 = p2(F4x, F4y);
+        const float2 S23 = add2(Fs2, Fs3);
+        const float2 dP = fma2(p2s(hh6), add2(F1, S23), mul2(H, M));
+        const float2 dM = mul2(p2s(h6), add2(fma2(p2s(2.0f), S23, F1), Fs4));
+        float2 Pn = P, Pc = p2(s.cX, s.cy), Mn = M, Mc = p2(s.cpx, s.cpy);
+        kahan2(Pn, Pc, dP);
+        kahan2(Mn, Mc, dM);
+        o = s;
+        o.X = Pn.x; o.y = Pn.y; o.cX = Pc.x; o.cy = Pc.y;
+        o.px = Mn.x; o.py = Mn.y; o.cpx = Mc.x; o.cpy = Mc.y;
+        kahan_add(o.z, o.cz, h * s.pz);
+        const float2 De = sub2(Pn, P4);
+        float Fex = F4x, Fey = F4y;
+        med_end<R, INTEG>(k, o.X, o.y, De.x, De.y, wr, wi, rr, ri, Fex, Fey, gpr, gpi, solved, st);
+        o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
+        if constexpr (gauss_of(INTEG)) { o.Fx = Fex; o.Fy = Fey; }
+        wrap_cell<R, INTEG>(o);
+        return;
+    }
     const R h2 = R(0.5) * h;
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     // stage 2 at r + h/2 p

@@ -555,64 +555,41 @@ __host__ __device__ constexpr double dp_ea(int l)
     return v;
 }
 
-// Coefficients of the Nystrom form for the stage loop: row j - 2 of kDpAA
-// holds (A A)_jl for stages j = 2..6 and (b A)_l for the solution (j = 7);
-// kDpC the nodes c_j.  The loop over the stages is kept rolled, with one
-// evaluation of W0 and the force in its body: unrolled, the seven inlined
+// Coefficients of the Nystrom form for the FP64 stage loop: row j - 2 of
+// kDpAA holds (A A)_jl for stages j = 2..6 and (b A)_l for the solution
+// (j = 7); kDpC the nodes c_j.  The loop over the stages is kept rolled, with
+// one evaluation of W0 and the force in its body: unrolled, the seven inlined
 // evaluations overflow the instruction cache (most issue slots were lost to
 // instruction fetch).
-#define RT_DPAA_ROW(j) \
-    {(float)dp_aa(j, 1), (float)dp_aa(j, 2), (float)dp_aa(j, 3), (float)dp_aa(j, 4), (float)dp_aa(j, 5), (float)dp_aa(j, 6)}
 #define RT_DPAA_ROWD(j) {dp_aa(j, 1), dp_aa(j, 2), dp_aa(j, 3), dp_aa(j, 4), dp_aa(j, 5), dp_aa(j, 6)}
-static __constant__ float kDpAAf[6][6] = {RT_DPAA_ROW(2), RT_DPAA_ROW(3), RT_DPAA_ROW(4),
-                                          RT_DPAA_ROW(5), RT_DPAA_ROW(6), RT_DPAA_ROW(7)};
 static __constant__ double kDpAAd[6][6] = {RT_DPAA_ROWD(2), RT_DPAA_ROWD(3), RT_DPAA_ROWD(4),
                                            RT_DPAA_ROWD(5), RT_DPAA_ROWD(6), RT_DPAA_ROWD(7)};
-#undef RT_DPAA_ROW
 #undef RT_DPAA_ROWD
-static __constant__ float kDpCf[6] = {(float)dp_c(2), (float)dp_c(3), (float)dp_c(4), (float)dp_c(5), (float)dp_c(6), 1.0f};
 static __constant__ double kDpCd[6] = {dp_c(2), dp_c(3), dp_c(4), dp_c(5), dp_c(6), 1.0};
 template <class R> __device__ __forceinline__ R dp_tab_aa(int r, int c);
-template <> __device__ __forceinline__ float dp_tab_aa<float>(int r, int c) { return kDpAAf[r][c]; }
 template <> __device__ __forceinline__ double dp_tab_aa<double>(int r, int c) { return kDpAAd[r][c]; }
-// The same coefficients for the running sums of dp45_step: row r of kDpP
-// holds (A A)_{r+2, q+1} for q = 0..6 (zero past the tableau, so that rows
-// up to 10 may be read), and kDpB, kDpEA, kDpE hold b_{q+1}, (e A)_{q+1}
-// and e_{q+1}.
+// The same coefficients for the running sums of the FP32 step, each value
+// twice (a packed pair for FFMA2): row r of kDpP2 holds (A A)_{r+2, q+1} for
+// q = 0..6 (zero past the tableau, so that rows up to 10 may be read); kDpB2,
+// kDpEA2 and kDpE2 hold b_{q+1}, (e A)_{q+1} and e_{q+1}; kDpC2 c_{q+2}.
 __host__ __device__ constexpr double dp_aap(int r, int q) { return (r + 2 <= 7 && q + 1 <= 6) ? dp_aa(r + 2, q + 1) : 0.0; }
-#define RT_DPP_ROW(T, r) {(T)dp_aap(r, 0), (T)dp_aap(r, 1), (T)dp_aap(r, 2), (T)dp_aap(r, 3), (T)dp_aap(r, 4), \
-                          (T)dp_aap(r, 5), (T)dp_aap(r, 6)}
-#define RT_DPP_TABLE(T) {RT_DPP_ROW(T, 0), RT_DPP_ROW(T, 1), RT_DPP_ROW(T, 2), RT_DPP_ROW(T, 3), RT_DPP_ROW(T, 4), \
-                         RT_DPP_ROW(T, 5), RT_DPP_ROW(T, 6), RT_DPP_ROW(T, 7), RT_DPP_ROW(T, 8), RT_DPP_ROW(T, 9), \
-                         RT_DPP_ROW(T, 10)}
-#define RT_DPV(T, f) {(T)f(1), (T)f(2), (T)f(3), (T)f(4), (T)f(5), (T)f(6), (T)f(7)}
 __host__ __device__ constexpr double dp_b(int l) { return dp_a(7, l); }
-static __constant__ float kDpPf[11][7] = RT_DPP_TABLE(float);
-static __constant__ double kDpPd[11][7] = RT_DPP_TABLE(double);
-static __constant__ float kDpBf[7] = RT_DPV(float, dp_b);
-static __constant__ double kDpBd[7] = RT_DPV(double, dp_b);
-static __constant__ float kDpEAf[7] = RT_DPV(float, dp_ea);
-static __constant__ double kDpEAd[7] = RT_DPV(double, dp_ea);
-static __constant__ float kDpEf[7] = RT_DPV(float, dp_e);
-static __constant__ double kDpEd[7] = RT_DPV(double, dp_e);
+#define RT_F2(v) {(float)(v), (float)(v)}
+#define RT_DPP_ROW(r) {RT_F2(dp_aap(r, 0)), RT_F2(dp_aap(r, 1)), RT_F2(dp_aap(r, 2)), RT_F2(dp_aap(r, 3)), \
+                       RT_F2(dp_aap(r, 4)), RT_F2(dp_aap(r, 5)), RT_F2(dp_aap(r, 6))}
+#define RT_DPV(f) {RT_F2(f(1)), RT_F2(f(2)), RT_F2(f(3)), RT_F2(f(4)), RT_F2(f(5)), RT_F2(f(6)), RT_F2(f(7))}
+static __constant__ float2 kDpP2[11][7] = {RT_DPP_ROW(0), RT_DPP_ROW(1), RT_DPP_ROW(2), RT_DPP_ROW(3), RT_DPP_ROW(4),
+                                           RT_DPP_ROW(5), RT_DPP_ROW(6), RT_DPP_ROW(7), RT_DPP_ROW(8), RT_DPP_ROW(9),
+                                           RT_DPP_ROW(10)};
+static __constant__ float2 kDpB2[7] = RT_DPV(dp_b);
+static __constant__ float2 kDpEA2[7] = RT_DPV(dp_ea);
+static __constant__ float2 kDpE2[7] = RT_DPV(dp_e);
+static __constant__ float2 kDpC2[6] = {RT_F2(dp_c(2)), RT_F2(dp_c(3)), RT_F2(dp_c(4)), RT_F2(dp_c(5)), RT_F2(dp_c(6)),
+                                       RT_F2(dp_c(7))};
 #undef RT_DPP_ROW
-#undef RT_DPP_TABLE
 #undef RT_DPV
-template <class R> struct DpTab;
-template <> struct DpTab<float> {
-    static __device__ __forceinline__ float p(int r, int q) { return kDpPf[r][q]; }
-    static __device__ __forceinline__ float b(int q) { return kDpBf[q]; }
-    static __device__ __forceinline__ float ea(int q) { return kDpEAf[q]; }
-    static __device__ __forceinline__ float e(int q) { return kDpEf[q]; }
-};
-template <> struct DpTab<double> {
-    static __device__ __forceinline__ double p(int r, int q) { return kDpPd[r][q]; }
-    static __device__ __forceinline__ double b(int q) { return kDpBd[q]; }
-    static __device__ __forceinline__ double ea(int q) { return kDpEAd[q]; }
-    static __device__ __forceinline__ double e(int q) { return kDpEd[q]; }
-};
+#undef RT_F2
 template <class R> __device__ __forceinline__ R dp_tab_c(int r);
-template <> __device__ __forceinline__ float dp_tab_c<float>(int r) { return kDpCf[r]; }
 template <> __device__ __forceinline__ double dp_tab_c<double>(int r) { return kDpCd[r]; }
 
 // One Dormand-Prince step of size h from s (W0 solved and force known at s)
@@ -691,74 +668,66 @@ __device__ __forceinline__ void dp45_step_table(const StepConst<R>& k, const Box
 }
 
 // The same step with running sums in place of the table of stage forces,
-// which the rolled stage loop indexes and so keeps in local memory.
+// which the rolled stage loop indexes and so keeps in local memory; FP32
+// only, with the sums' (x, y) components in packed pairs.
 template <class R, int INTEG>
 __device__ __forceinline__ void dp45_step_sums(const StepConst<R>& k, const Box<R>& s, R h, Box<R>& o, R e[4],
                                                LaneStats& st)
 {
-    R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
-    R Xp = s.X, yp = s.y;
-    R gpr = R(0), gpi = R(0);
-    const R hpx = h * s.px, hpy = h * s.py, hh = h * h;
-    // Running sums instead of a table of the stage forces (which a rolled
-    // stage loop would keep in local memory): slot m holds the position sum
-    // sum_l (A A)_{j+m, l} F_l of stage j + m over the forces known so far;
-    // M, EA and E the momentum sum b.F and the error sums (e A).F and e.F.
-    R Sx[6], Sy[6];
+    static_assert(sizeof(R) == 4, "the running-sum step is the FP32 one");
+    float wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
+    float gpr = 0.0f, gpi = 0.0f;
+    const float2 P0 = p2(s.X, s.y), H = p2s(h), HH = p2s(h * h);
+    const float2 HP = mul2(H, p2(s.px, s.py));
+    // slot m holds the position sum sum_l (A A)_{j+m, l} F_l of stage j + m
+    // over the forces known so far; Mv, EAv and Ev the momentum sum b.F and
+    // the error sums (e A).F and e.F
+    float2 S[6];
 #pragma unroll
-    for (int m = 0; m < 6; ++m) Sx[m] = Sy[m] = R(0);
-    R Mx = R(0), My = R(0), EAx = R(0), EAy = R(0), Ex = R(0), Ey = R(0);
-    R Fcx = s.Fx, Fcy = s.Fy;                          // the newest force (stage j - 1)
+    for (int m = 0; m < 6; ++m) S[m] = p2s(0.0f);
+    float2 Mv = p2s(0.0f), EAv = p2s(0.0f), Ev = p2s(0.0f);
+    float2 Fc = p2(s.Fx, s.Fy);                        // the newest force (stage j - 1)
+    float2 Pp = P0;                                    // the previous stage point
 #pragma unroll 1
     for (int j = 2; j <= 7; ++j) {
-        const int q = j - 2;                           // its index
-        const R b = DpTab<R>::b(q), ea = DpTab<R>::ea(q), ee = DpTab<R>::e(q);
-        Mx += b * Fcx; My += b * Fcy;
-        EAx += ea * Fcx; EAy += ea * Fcy;
-        Ex += ee * Fcx; Ey += ee * Fcy;
+        const int q = j - 2;                           // the newest force's index
+        Mv = fma2(kDpB2[q], Fc, Mv);
+        EAv = fma2(kDpEA2[q], Fc, EAv);
+        Ev = fma2(kDpE2[q], Fc, Ev);
 #pragma unroll
-        for (int m = 0; m < 6; ++m) {
-            const R a = DpTab<R>::p(q + m, q);
-            Sx[m] += a * Fcx;
-            Sy[m] += a * Fcy;
-        }
-        R Xs, Ys;
+        for (int m = 0; m < 6; ++m) S[m] = fma2(kDpP2[q + m][q], Fc, S[m]);
+        float2 Ps;
         if (j < 7) {
-            Xs = s.X + (dp_tab_c<R>(j - 2) * hpx + hh * Sx[0]);
-            Ys = s.y + (dp_tab_c<R>(j - 2) * hpy + hh * Sy[0]);
+            Ps = add2(P0, fma2(kDpC2[q], HP, mul2(HH, S[0])));
         } else {
             o = s;
-            kahan_add(o.X, o.cX, hpx + hh * Sx[0]);
-            kahan_add(o.y, o.cy, hpy + hh * Sy[0]);
+            float2 Pn = P0, Pc = p2(s.cX, s.cy), Mn = p2(s.px, s.py), Mc = p2(s.cpx, s.cpy);
+            kahan2(Pn, Pc, fma2(HH, S[0], HP));
+            kahan2(Mn, Mc, mul2(H, Mv));
             kahan_add(o.z, o.cz, h * s.pz);
-            kahan_add(o.px, o.cpx, h * Mx);
-            kahan_add(o.py, o.cpy, h * My);
-            Xs = o.X;
-            Ys = o.y;
+            o.X = Pn.x; o.y = Pn.y; o.cX = Pc.x; o.cy = Pc.y;
+            o.px = Mn.x; o.py = Mn.y; o.cpx = Mc.x; o.cpy = Mc.y;
+            Ps = Pn;
         }
-        R Fnx, Fny;
-        med_stage<R, INTEG>(k, Xs, Ys, Xs - Xp, Ys - yp, wr, wi, rr, ri, Fcx, Fcy, Fnx, Fny, gpr, gpi, st);
-        Fcx = Fnx;
-        Fcy = Fny;
-        Xp = Xs;
-        yp = Ys;
+        const float2 D = sub2(Ps, Pp);
+        float Fnx, Fny;
+        med_stage<R, INTEG>(k, Ps.x, Ps.y, D.x, D.y, wr, wi, rr, ri, Fc.x, Fc.y, Fnx, Fny, gpr, gpi, st);
+        Fc = p2(Fnx, Fny);
+        Pp = Ps;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            Sx[m] = Sx[m + 1];
-            Sy[m] = Sy[m + 1];
-        }
-        Sx[5] = Sy[5] = R(0);
+        for (int m = 0; m < 5; ++m) S[m] = S[m + 1];
+        S[5] = p2s(0.0f);
     }
     // the force at the solution (stage 7) enters the momentum error only
-    Ex += DpTab<R>::e(6) * Fcx;
-    Ey += DpTab<R>::e(6) * Fcy;
+    Ev = fma2(kDpE2[6], Fc, Ev);
     o.wr = wr; o.wi = wi; o.rr = rr; o.ri = ri;
-    o.Fx = Fcx;
-    o.Fy = Fcy;
-    e[0] = hh * EAx;
-    e[1] = hh * EAy;
-    e[2] = h * Ex;
-    e[3] = h * Ey;
+    o.Fx = Fc.x;
+    o.Fy = Fc.y;
+    const float2 EA = mul2(HH, EAv), E = mul2(H, Ev);
+    e[0] = EA.x;
+    e[1] = EA.y;
+    e[2] = E.x;
+    e[3] = E.y;
     wrap_cell<R, INTEG>(o);
 }
 

@@ -241,6 +241,25 @@ int rt_scene_set_launch(rt_scene* scene, int32_t variant, int32_t min_active);
 int rt_scene_get_launch(rt_scene* scene, int32_t* variant, int32_t* min_active, int32_t* grid);
 
 /*
+ * rt_scene_set_wait_limit: bounds of the waits of the wavefront loop
+ * (variant 3) on its per-block work queues, for this scene's later renders.
+ * The paper has no counterpart: this is the runtime's failure detection.
+ *   spin_limit  attempts (each followed by a short sleep) a wait makes before
+ *               the launch gives it up: 1..2^24; 0 restores the default 2^24
+ *               (about a second of waiting)
+ *   hold_lock   0 for normal renders; nonzero starts every block with its
+ *               queue lock taken and never released, so that every wait of
+ *               the launch runs out after spin_limit attempts.  This makes a
+ *               bounded wait expire on purpose, for tests of failure
+ *               detection: no GPU fault is involved, every block returns,
+ *               the image is left incomplete and rt_scene_stats reports
+ *               RT_ETIMEDOUT with the timeouts counted in sched_timeouts.
+ * Host only (takes effect at the next render).  Returns RT_EINVAL for a
+ * spin_limit out of range.
+ */
+int rt_scene_set_wait_limit(rt_scene* scene, int32_t spin_limit, int32_t hold_lock);
+
+/*
  * rt_scene_autotune: time the scene's launch configurations (every
  * register-budget variant compiled for its precision and integrator, times
  * min_active in {12, 16, 20, 24, 28}; median of `trials` full renders into
@@ -389,7 +408,8 @@ int rt_xcorr(const float* d_f, const float* d_g, int32_t height, int32_t width, 
  * RT_EINVAL.
  * The first call on a device looks up the array's device address (once per
  * device, with that device current); make that first call before any stream
- * capture.  Every call shares the one array, so calls that overlap on the GPU
+ * capture.  The address is kept for the life of the process, so do not call
+ * this entry point on a device after cudaDeviceReset of that device.  Every call shares the one array, so calls that overlap on the GPU
  * (on different streams, or from different threads) race; each call
  * overwrites all scratch it reads, so nothing needs clearing.  Asynchronous.
  */

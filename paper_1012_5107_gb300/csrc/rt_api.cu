@@ -61,6 +61,7 @@ struct rt_scene {
     size_t branch_cap;
     cudaEvent_t done;
     bool rendered;
+    WaitLimit wait;           // bounds of the wavefront loop's waits (rt_scene_set_wait_limit)
 };
 
 static int current_device(int* dev)
@@ -298,6 +299,7 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     int bps = 0;
     s->variant = kDefaultVariant;
     s->min_active = kMinActive;
+    s->wait = WaitLimit{kDefaultWaitSpin, 0};
     cudaError_t e = desc->mirror == RT_MIRROR_GAUSS ? gauss_upload() : cudaSuccess;
     if (e == cudaSuccess) e = render_occupancy(desc->precision, render_mode(*desc), s->variant, desc->flags != 0, &bps);
     int nsm = 0;
@@ -387,7 +389,7 @@ static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float
     }
     if (nwork > 0)
         RT_CK(launch_render(sc, s->desc.precision, s->variant, s->min_active, d_rgb, d_rgb8, d_rec, s->d_counters,
-                            s->grid, ss, st));
+                            s->grid, ss, s->wait, st));
     RT_CK(cudaEventRecord(s->done, st));
     s->rendered = true;
     return RT_OK;
@@ -514,6 +516,17 @@ int rt_scene_set_launch(rt_scene* s, int32_t variant, int32_t min_active)
         s->grid = bps * s->nsm;
     }
     if (min_active > 0) s->min_active = min_active;
+    return RT_OK;
+}
+
+int rt_scene_set_wait_limit(rt_scene* s, int32_t spin_limit, int32_t hold_lock)
+{
+    g_err[0] = 0;
+    RT_REQ(s, "scene is NULL");
+    RT_REQ(spin_limit >= 0 && spin_limit <= kDefaultWaitSpin, "spin_limit must be 0 (default) or 1..%d",
+           kDefaultWaitSpin);
+    s->wait.spin = spin_limit ? spin_limit : kDefaultWaitSpin;
+    s->wait.hold = hold_lock ? 1 : 0;
     return RT_OK;
 }
 

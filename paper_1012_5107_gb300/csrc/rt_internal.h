@@ -57,9 +57,16 @@ size_t branch_queue_bytes(int precision, int grid);
 constexpr size_t kScratchBytesPerSample = 3 * sizeof(float);
 constexpr size_t kScratchBytesPerPixel = sizeof(int);
 
+// Bounds of the wavefront loop's waits on its work queues: attempts per wait
+// and whether every block starts with its queue lock held (rt_scene_set_wait_limit).
+constexpr int kDefaultWaitSpin = 1 << 24;
+struct WaitLimit {
+    int spin;
+    int hold;
+};
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
                           rt_ray_record* rec, unsigned long long* counters, int grid, const SampleScratch& ss,
-                          cudaStream_t stream);
+                          const WaitLimit& wl, cudaStream_t stream);
 cudaError_t launch_medium(int precision, double kA, double Lambda, const double* xy, int64_t n, double* out,
                           cudaStream_t stream);
 

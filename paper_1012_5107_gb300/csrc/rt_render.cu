@@ -68,7 +68,7 @@ static cudaError_t occupancy_t(int variant, bool opt, int* bps)
 template <class R, int INTEG>
 static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, float* rgb, uint8_t* rgb8,
                             rt_ray_record* rec, unsigned long long* counters, int grid, const SampleScratch& ss,
-                            cudaStream_t stream)
+                            const WaitLimit& wl, cudaStream_t stream)
 {
     if (variant == kVariantWave) {
         // scenes with options (RT_FLAG_*) take the options build of the loop;
@@ -78,14 +78,14 @@ static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, flo
                 const cudaError_t e = wave_prepare<R, INTEG, true>();
                 if (e != cudaSuccess) return e;
                 wave_kernel<R, INTEG, true><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
-                    sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br);
+                    sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br, WaveWait{wl.spin, wl.hold});
                 return cudaGetLastError();
             }
         }
         const cudaError_t e = wave_prepare<R, INTEG, false>();
         if (e != cudaSuccess) return e;
         wave_kernel<R, INTEG, false><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
-            sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br);
+            sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br, WaveWait{wl.spin, wl.hold});
         return cudaGetLastError();
     }
     if constexpr (integ_of(INTEG) == RT_RK4T || gauss_of(INTEG)) {
@@ -188,11 +188,11 @@ cudaError_t render_occupancy(int precision, int integrator, int variant, bool op
 
 cudaError_t launch_render(const DevScene& sc, int precision, int variant, int min_active, float* rgb, uint8_t* rgb8,
                           rt_ray_record* rec, unsigned long long* counters, int grid, const SampleScratch& ss,
-                          cudaStream_t stream)
+                          const WaitLimit& wl, cudaStream_t stream)
 {
     constexpr int G = kModeGauss;
     const int mode = sc.integrator | (sc.mirror == RT_MIRROR_GAUSS ? G : 0);
-#define RT_LAUNCH(RR, M) return launch_t<RR, M>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, stream)
+#define RT_LAUNCH(RR, M) return launch_t<RR, M>(sc, variant, min_active, rgb, rgb8, rec, counters, grid, ss, wl, stream)
     if (precision == RT_FP64) {
         switch (mode) {
             case RT_DP45: RT_LAUNCH(double, RT_DP45);

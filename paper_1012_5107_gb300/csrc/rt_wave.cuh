@@ -25,8 +25,8 @@
 //
 // The queues are rings of 16-bit pool indices guarded by a block-level lock
 // (an atomic flag in shared memory) that one lane per warp takes for a few
-// dozen cycles per task; every wait on it is bounded and a timeout is counted
-// in counters[kCounters - 1] (reported as an error by the host).
+// dozen cycles per task; every wait on it is bounded (WaveWait) and a timeout
+// is counted in counters[kCounters - 1] (reported as an error by the host).
 #pragma once
 
 #include "rt_trace.cuh"
@@ -35,7 +35,7 @@ namespace grt {
 
 constexpr int kWaveBlock = 256;
 constexpr int kWaveTaskSteps = 256;          // step cap of one integration task
-constexpr int kWaveSpin = 1 << 24;           // attempts (with a short sleep) before a wait gives up
+constexpr int kWaveSpin = kDefaultWaitSpin;  // attempts (with a short sleep) before a wait gives up
 
 // Pixels in flight per block: more than the block's lanes, so that a warp
 // always finds work while the other warps hold theirs.
@@ -68,9 +68,18 @@ struct WaveCtl {
 enum : int { WT_WAIT = 0, WT_INT = 1, WT_SRV = 2, WT_DONE = 3, WT_ERR = 4 };
 enum : int { WD_NONE = 0, WD_IN = 1, WD_SRV = 2, WD_FREE = 3 };
 
-__device__ __forceinline__ bool wave_acquire(int* lock)
+// How the waits of a launch are bounded: `spin` attempts per wait (kWaveSpin
+// unless the scene asks for fewer) and, with `hold` set, every block starts
+// with its queue lock taken, so that every wait runs out and the launch ends
+// with the timeouts counted (a test of failure detection; nothing faults).
+struct WaveWait {
+    int spin;
+    int hold;
+};
+
+__device__ __forceinline__ bool wave_acquire(int* lock, int spin)
 {
-    for (int it = 0; it < kWaveSpin; ++it) {
+    for (int it = 0; it < spin; ++it) {
         if (atomicCAS(lock, 0, 1) == 0) {
             __threadfence_block();
             return true;
@@ -91,7 +100,7 @@ __device__ __forceinline__ void wave_release(int* lock)
 // false if the lock could not be taken.
 template <int P>
 __device__ __forceinline__ bool wave_push(WaveCtl& Q, short* inq, short* svq, short* frq, unsigned lane, int p,
-                                          int dest)
+                                          int dest, int spin)
 {
     __threadfence_block();      // this lane's pool writes before its index is published
     const unsigned mi = __ballot_sync(0xffffffffu, dest == WD_IN);
@@ -100,7 +109,7 @@ __device__ __forceinline__ bool wave_push(WaveCtl& Q, short* inq, short* svq, sh
     if ((mi | ms | mf) == 0u) return true;
     int ok = 1, ti = 0, ts = 0, tf = 0;
     if (lane == 0) {
-        ok = wave_acquire(&Q.lock) ? 1 : 0;
+        ok = wave_acquire(&Q.lock, spin) ? 1 : 0;
         if (ok) {
             ti = Q.in_head + Q.in_cnt;
             ts = Q.sv_head + Q.sv_cnt;
@@ -161,7 +170,7 @@ __device__ __forceinline__ void wave_finish_sample(const Src& src, const DevScen
 }
 
 template <class R, int INTEG, bool OPT, class Src>
-__device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* counters, int min_active)
+__device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* counters, int min_active, WaveWait ww)
 {
     constexpr int P = WavePool<R>::P;
     extern __shared__ __align__(16) unsigned char wave_smem[];
@@ -183,7 +192,7 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
         frq[p] = (short)p;
     }
     if (threadIdx.x == 0) {
-        Q.lock = 0;
+        Q.lock = ww.hold ? 1 : 0;
         Q.in_head = Q.in_cnt = Q.sv_head = Q.sv_cnt = 0;
         Q.fr_cnt = P;
         Q.exhausted = 0;
@@ -206,7 +215,7 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
         // ---- take a task (the leader decides under the lock) ----
         int task = WT_WAIT, m1 = 0, m2 = 0, b1 = 0, b2 = 0, locked = 0;
         if (lane == 0) {
-            if (!wave_acquire(&Q.lock)) {
+            if (!wave_acquire(&Q.lock, ww.spin)) {
                 task = WT_ERR;
             } else {
                 locked = 1;
@@ -257,7 +266,7 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
         if (task == WT_ERR) { failed = true; break; }
         if (task == WT_DONE) break;
         if (task == WT_WAIT) {
-            if (++idle > kWaveSpin) { failed = true; break; }
+            if (++idle > ww.spin) { failed = true; break; }
             __nanosleep(256);
             continue;
         }
@@ -360,7 +369,7 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
 #if RT_PROFILE
         prof[task == WT_INT ? 0 : 1] += (unsigned long long)(clock64() - t_task);
 #endif
-        if (!wave_push<P>(Q, inq, svq, frq, lane, p, dest)) { failed = true; break; }
+        if (!wave_push<P>(Q, inq, svq, frq, lane, p, dest, ww.spin)) { failed = true; break; }
     }
 #if RT_PROFILE
     prof[3] = (unsigned long long)(clock64() - t_start);
@@ -404,10 +413,10 @@ __global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_kernel(
                                                             float* __restrict__ rgb, uint8_t* __restrict__ rgb8,
                                                             rt_ray_record* rec, unsigned long long* counters,
                                                             int min_active, float* samp_col, int* pix_cnt,
-                                                            void* branches)
+                                                            void* branches, WaveWait ww)
 {
     const OneScene src{sc, rgb, rgb8, rec, samp_col, pix_cnt, branches};
-    wave_loop<R, INTEG, OPT>(src, counters, min_active);
+    wave_loop<R, INTEG, OPT>(src, counters, min_active, ww);
 }
 
 template <class R, int INTEG, bool OPT>
@@ -417,7 +426,7 @@ __global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_batch_k
     void* branches, unsigned long long* counters, int min_active)
 {
     const ManyScenes src{scenes, offsets, soffsets, rgbs, n, total, total_samples, samp_col, pix_cnt, branches};
-    wave_loop<R, INTEG, OPT>(src, counters, min_active);
+    wave_loop<R, INTEG, OPT>(src, counters, min_active, WaveWait{kWaveSpin, 0});
 }
 
 }  // namespace grt

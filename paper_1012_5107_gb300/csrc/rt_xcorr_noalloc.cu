@@ -13,7 +13,10 @@
 // which loads the library holds until the process exits.  Host code must not pass the array's name to a
 // kernel: in host code it names a host-side stand-in, not device memory.  The
 // device address is taken with cudaGetSymbolAddress, once per device, with
-// that device current, by the first call of rt_xcorr_noalloc on the device.
+// that device current, by the first call of rt_xcorr_noalloc on the device,
+// and kept for the life of the process: a cudaDeviceReset of that device
+// invalidates it (the module is loaded again, possibly elsewhere), so the
+// entry point must not be used on a device after resetting it.
 #include <cstdio>
 #include <mutex>
 
@@ -61,6 +64,7 @@ using namespace grt;
 extern "C" int rt_xcorr_noalloc(const float* d_f, const float* d_g, int32_t height, int32_t width, int32_t channels,
                                 const double* fov_deg, int32_t n_fov, double hfov_deg, double* d_out, void* stream)
 {
+    set_error("%s", "");             // no stale message from an earlier call
     if (!d_f || !d_g || !d_out || !fov_deg) { set_error("null pointer argument"); return RT_EINVAL; }
     if (height < 1 || width < 1) { set_error("height and width must be >= 1"); return RT_EINVAL; }
     if (channels < 1 || channels > 4) { set_error("channels must be 1..4"); return RT_EINVAL; }

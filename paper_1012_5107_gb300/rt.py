@@ -77,7 +77,8 @@ class Stats(C.Structure):
 _lib = None
 
 EXPORTS = ["rt_create_scene", "rt_destroy_scene", "rt_render", "rt_render_pixels", "rt_render_host",
-           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_scene_autotune",
+           "rt_scene_stats", "rt_scene_set_launch", "rt_scene_get_launch", "rt_scene_set_wait_limit",
+           "rt_scene_autotune",
            "rt_batch_create", "rt_batch_destroy", "rt_batch_render", "rt_batch_stats", "rt_batch_set_launch",
            "rt_batch_get_launch", "rt_batch_autotune", "rt_batch_update",
            "rt_validate_desc", "rt_request_bytes", "rt_server_create", "rt_server_destroy", "rt_submit", "rt_poll",
@@ -104,6 +105,7 @@ def lib() -> C.CDLL:
     L.rt_scene_stats.argtypes = [vp, C.POINTER(Stats)]
     L.rt_scene_set_launch.argtypes = [vp, C.c_int32, C.c_int32]
     L.rt_scene_get_launch.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
+    L.rt_scene_set_wait_limit.argtypes = [vp, C.c_int32, C.c_int32]
     L.rt_scene_autotune.argtypes = [vp, vp, C.c_int32, vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.rt_batch_create.argtypes = [C.POINTER(vp), C.c_int32, C.POINTER(vp)]
     L.rt_batch_destroy.argtypes = [vp]
@@ -217,6 +219,12 @@ class Scene:
     def set_launch(self, variant: int = -1, min_active: int = 0):
         _check(lib().rt_scene_set_launch(self._h, variant, min_active))
 
+    def set_wait_limit(self, spin_limit: int = 0, hold_lock: bool = False):
+        """rt_scene_set_wait_limit: attempts per wait of the wavefront loop's queues
+        (0: the default) and, with hold_lock, make every wait of the next renders
+        run out (failure-detection tests)."""
+        _check(lib().rt_scene_set_wait_limit(self._h, int(spin_limit), 1 if hold_lock else 0))
+
     def get_launch(self) -> dict:
         v, m, g = C.c_int32(), C.c_int32(), C.c_int32()
         _check(lib().rt_scene_get_launch(self._h, C.byref(v), C.byref(m), C.byref(g)))
@@ -228,10 +236,15 @@ class Scene:
         _check(lib().rt_scene_autotune(self._h, _ptr(rgb), trials, _stream(stream), C.byref(v), C.byref(m)))
         return {"variant": v.value, "min_active": m.value}
 
-    def stats(self) -> dict:
+    def stats(self, check: bool = True) -> dict:
+        """Counters of the last render (rt_scene_stats).  With check=False a
+        render that gave up bounded waits (RT_ETIMEDOUT) still returns its
+        counters, with the return code under "rc", instead of raising."""
         s = Stats()
-        _check(lib().rt_scene_stats(self._h, C.byref(s)))
-        return _stats_dict(s)
+        rc = lib().rt_scene_stats(self._h, C.byref(s))
+        if check or rc not in (RT_OK, RT_ETIMEDOUT):
+            _check(rc)
+        return dict(_stats_dict(s), rc=rc)
 
 
 def _stats_dict(s: Stats) -> dict:

@@ -9,6 +9,7 @@ import math
 import numpy as np
 import pytest
 
+from conditioning import scene_entry
 from paper_1012_5107_gb300 import inputs
 
 pytestmark = pytest.mark.gpu
@@ -59,26 +60,6 @@ def gpu_render(rt, torch, p, records=True, tex=None, variant=None, min_active=0)
 # the oracle itself and reported apart from the parity bar.
 EPS32 = 3e-7
 PERTURB = 1e-7
-
-
-def scene_entry(p, org, d):
-    """Parameter t at which the camera ray org + t d first reaches the scene:
-    the cloak box (slab test) or the band y <= A of the grating, whichever
-    comes first; None if it reaches neither."""
-    lam = p["Lambda"]
-    ts = []
-    if d[1] < 0.0:
-        ts.append((max(p["A"], 1e-6 * lam) - org[1]) / d[1])
-    if p["cloak"]:
-        lo = np.array([-p["E"] / 2, -p["A"], -p["E"] / 2])
-        hi = np.array([p["E"] / 2, p["H"] - p["A"], p["E"] / 2])
-        with np.errstate(divide="ignore", invalid="ignore"):
-            t1, t2 = (lo - org) / d, (hi - org) / d
-        tn, tf = np.minimum(t1, t2).max(), np.maximum(t1, t2).min()
-        if tn <= tf and tn > 0:
-            ts.append(tn)
-    ts = [t for t in ts if t > 0]
-    return min(ts) if ts else None
 
 
 def sensitivity(orc, p, pix, spp, o_rec, tex=None):

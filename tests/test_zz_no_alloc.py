@@ -52,3 +52,8 @@ def test_noalloc_rejects_oversized_images(rt):
         rt.xcorr_noalloc(f, f, [50.0], 50.0)
     assert e.value.code == rt.RT_EINVAL
     assert "scratch" in str(e.value)
+    # a successful call afterwards leaves no stale message behind
+    g = torch.ones((8, 8, 3), dtype=torch.float32, device="cuda")
+    rt.xcorr_noalloc(g, g, [50.0], 50.0)
+    torch.cuda.synchronize()
+    assert rt.lib().rt_last_error() == b""

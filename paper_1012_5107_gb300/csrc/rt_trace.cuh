@@ -65,6 +65,7 @@ template <class R>
 struct Cold {
     R cx, X, y, z;            // air: position, x = cx + X
     R dx, dy, dz;             // air: unit direction
+    float dl[3];              // FP32 path: the rounding residual of a direction formed in FP64 (else 0)
     R g1[EV_COUNT];           // event functions at the end of a step that crossed a surface
     R hs;                     // size of that step
     int64_t work;             // output slot of the pixel in its scene's arrays
@@ -83,6 +84,41 @@ struct Cold {
 };
 
 enum : int { MED_AIR = 0, MED_BOX = 1, MED_PLATE = 2 };
+
+// The air direction in FP64.  Directions formed in FP64 (the camera ray, a
+// reflection or refraction) keep their FP32 rounding residual in dl, so that
+// the next FP64 step -- Snell's law at a box face, a mirror reflection --
+// starts from the direction as it was formed: Snell's law at a shallow entry
+// multiplies a direction error by |p_t| / |p_n|, and the rays that leave the
+// cloak and meet the bare grating again amplify it further.
+template <class R>
+__device__ __forceinline__ void air_dir(const Cold<R>& C, double d[3])
+{
+    d[0] = (double)C.dx + (double)C.dl[0];
+    d[1] = (double)C.dy + (double)C.dl[1];
+    d[2] = (double)C.dz + (double)C.dl[2];
+}
+
+template <class R>
+__device__ __forceinline__ void set_air_dir(Cold<R>& C, double x, double y, double z)
+{
+    C.dx = (R)x;
+    C.dy = (R)y;
+    C.dz = (R)z;
+    C.dl[0] = (float)(x - (double)C.dx);
+    C.dl[1] = (float)(y - (double)C.dy);
+    C.dl[2] = (float)(z - (double)C.dz);
+}
+
+// A direction known only in the path's precision (no residual).
+template <class R>
+__device__ __forceinline__ void set_air_dir_r(Cold<R>& C, R x, R y, R z)
+{
+    C.dx = x;
+    C.dy = y;
+    C.dz = z;
+    C.dl[0] = C.dl[1] = C.dl[2] = 0.0f;
+}
 constexpr int kMaxBranches = 8;      // Fresnel branches followed per camera sample
 
 // A Fresnel branch waiting to be traced: where it starts, its momentum (unit
@@ -948,9 +984,7 @@ __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
     C.X = (R)(Px - cxd);
     C.y = (R)(sc.C[1] + t * d[1]);
     C.z = (R)(sc.C[2] + t * d[2]);
-    C.dx = (R)d[0];
-    C.dy = (R)d[1];
-    C.dz = (R)d[2];
+    set_air_dir(C, d[0], d[1], d[2]);
 }
 
 // Straight line against the flat mirror y = 0.
@@ -1225,7 +1259,8 @@ __device__ __forceinline__ void finish_sample(const DevScene& sc, Cold<R>& C, in
     if (rec) {
         rt_ray_record* o = rec + C.work * sc.spp + C.sample;
         const double pos[3] = {(double)C.cx + (double)C.X, (double)C.y, (double)C.z};
-        const double d[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+        double d[3];
+        air_dir(C, d);
         const double l = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
         for (int a = 0; a < 3; ++a) {
             o->pos[a] = pos[a] * sc.Lambda;
@@ -1249,9 +1284,7 @@ __device__ __forceinline__ void box_to_air(Cold<R>& C, const Box<R>& b, const R 
     C.y = b.y;
     C.z = b.z;
     const R il = R(1) / Mth<R>::sqrt_(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
-    C.dx = d[0] * il;
-    C.dy = d[1] * il;
-    C.dz = d[2] * il;
+    set_air_dir_r(C, d[0] * il, d[1] * il, d[2] * il);
 }
 
 // Inside the homogeneous plate of RT_FLAG_PLATE (index 1 + kA on the flat
@@ -1283,7 +1316,7 @@ __device__ bool plate_traverse(const DevScene& sc, Cold<R>& C, double P[3], doub
             const double cxd = rint(P[0]);
             const double ql = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
             C.cx = (R)cxd; C.X = (R)(P[0] - cxd); C.y = (R)P[1]; C.z = (R)P[2];
-            C.dx = (R)(q[0] / ql); C.dy = (R)(q[1] / ql); C.dz = (R)(q[2] / ql);
+            set_air_dir(C, q[0] / ql, q[1] / ql, q[2] / ql);
             finish_sample<R, OPT>(sc, C, steps, C.bounces > sc.max_bounces ? RT_RAY_MAX_BOUNCES : RT_RAY_NAN, phase, rec);
             return false;
         }
@@ -1313,9 +1346,7 @@ __device__ bool plate_traverse(const DevScene& sc, Cold<R>& C, double P[3], doub
         if (opt_flags<OPT>(sc) & RT_FLAG_FRESNEL)
             fresnel_split(C, fresnel_R(sc.plate_n, 1.0, pn, pout), MED_PLATE, C.cx, C.X, C.y, C.z,
                           q[0] - 2.0 * pn * N[0], q[1] - 2.0 * pn * N[1], q[2] - 2.0 * pn * N[2], hit, steps);
-        C.dx = (R)(pt[0] + pout * N[0]);
-        C.dy = (R)(pt[1] + pout * N[1]);
-        C.dz = (R)(pt[2] + pout * N[2]);
+        set_air_dir(C, pt[0] + pout * N[0], pt[1] + pout * N[1], pt[2] + pout * N[2]);
         return true;
     }
 }
@@ -1330,7 +1361,8 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
         // a Fresnel branch that starts inside the plate: C holds its position and momentum
         C.in_plate = 0;
         double P[3] = {(double)C.cx + (double)C.X, (double)C.y, (double)C.z};
-        double q[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+        double q[3];
+        air_dir(C, q);
         if (!plate_traverse<R, OPT>(sc, C, P, q, steps, phase, rec)) return;
         surf = EV_NONE;
     }
@@ -1348,7 +1380,8 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             advance(C, tb);
             R Nf[3];
             face_normal(face, Nf);
-            const double d[3] = {(double)C.dx, (double)C.dy, (double)C.dz};
+            double d[3];
+            air_dir(C, d);
             const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
             const double pn = d[0] * N[0] + d[1] * N[1] + d[2] * N[2];
             double pt[3];
@@ -1380,14 +1413,21 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
             med_solve<R, INTEG>(k, b.X, b.y, b.wr, b.wi, b.rr, b.ri, b.Fx, b.Fy, st);
             // Snell's law in FP64 (a few operations per entry): sqrt(n^2 - |p_t|^2)
             // is ill-conditioned near grazing incidence; the index is scaled
-            // by idx_scale in the referenced cloak
-            const double rr = (double)b.rr, ri = (double)b.ri;
-            double n2 = rr * rr + ri * ri;
+            // by idx_scale in the referenced cloak.  The grating's n^2 =
+            // 1/|1 + W0|^2 is formed in FP64 from W0: near the top of the box
+            // |W0| is ~1e-6, and 1 + W0 rounded to FP32 would leave n with a
+            // relative error of 6e-8, which the shallow entries of the
+            // camera rays turn into 2e-7 of momentum
+            double n2;
+            if constexpr (gauss_of(INTEG)) {
+                n2 = (double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri;
+            } else {
+                const double ar = 1.0 + (double)b.wr, ai = (double)b.wi;
+                n2 = 1.0 / (ar * ar + ai * ai);
+            }
             if (opt_flags<OPT>(sc) & RT_FLAG_REFERENCED) n2 *= sc.idx_scale * sc.idx_scale;
             if (n2 < pt2) {      // total reflection off the outside of the box
-                C.dx = (R)(d[0] - 2.0 * pn * N[0]);
-                C.dy = (R)(d[1] - 2.0 * pn * N[1]);
-                C.dz = (R)(d[2] - 2.0 * pn * N[2]);
+                set_air_dir(C, d[0] - 2.0 * pn * N[0], d[1] - 2.0 * pn * N[1], d[2] - 2.0 * pn * N[2]);
                 C.bounces++;
                 surf = EV_NONE;
                 continue;
@@ -1397,11 +1437,16 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                 fresnel_split(C, fresnel_R(1.0, sqrt(n2), pn, pin), MED_AIR, C.cx, C.X, C.y, C.z,
                               d[0] - 2.0 * pn * N[0], d[1] - 2.0 * pn * N[1], d[2] - 2.0 * pn * N[2], EV_NONE, steps);
             // the momentum |p| = n inside; the time form carries v = p / n^2
+            // (the FP32 path keeps the rounding of p_x, p_y in their
+            // compensation terms, which hold p - exact)
             const double iv = (integ_of(INTEG) == RT_RK4T) ? 1.0 / n2 : 1.0;
-            b.px = (R)((pt[0] - pin * N[0]) * iv);
-            b.py = (R)((pt[1] - pin * N[1]) * iv);
+            const double qx = (pt[0] - pin * N[0]) * iv, qy = (pt[1] - pin * N[1]) * iv;
+            b.px = (R)qx;
+            b.py = (R)qy;
             b.pz = (R)((pt[2] - pin * N[2]) * iv);
-            b.cX = b.cy = b.cz = b.cpx = b.cpy = R(0);
+            b.cX = b.cy = b.cz = R(0);
+            b.cpx = (R)((double)b.px - qx);
+            b.cpy = (R)((double)b.py - qy);
             b.hc = k.h;
             med_force<R, INTEG>(k, b);
             surf = face;
@@ -1430,13 +1475,15 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                     ny = 1.0 - (double)k.kA * (double)cs;
                 }
                 const double il = 1.0 / sqrt(nx * nx + ny * ny);
-                const double pn = ((double)C.dx * nx + (double)C.dy * ny) * il;
-                C.dx = (R)((double)C.dx - 2.0 * pn * nx * il);
-                C.dy = (R)((double)C.dy - 2.0 * pn * ny * il);
+                double d[3];
+                air_dir(C, d);
+                const double pn = (d[0] * nx + d[1] * ny) * il;
+                set_air_dir(C, d[0] - 2.0 * pn * nx * il, d[1] - 2.0 * pn * ny * il, d[2]);
             } else {
                 advance(C, tm);
                 C.y = R(0);
                 C.dy = -C.dy;
+                C.dl[1] = -C.dl[1];
             }
             C.bounces++;
             surf = EV_GRATING;
@@ -1490,13 +1537,27 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     C.events++;
     C.nevents++;
     if (ev_best == EV_GRATING) {
-        // mirror reflection about grad v / |grad v| = (Im r, Re r) / |r|
-        const R il = R(1) / Mth<R>::sqrt_(b.rr * b.rr + b.ri * b.ri);
-        const R nx = b.ri * il, ny = b.rr * il;
-        const R pn = b.px * nx + b.py * ny;
-        b.px -= R(2) * pn * nx;
-        b.py -= R(2) * pn * ny;
-        b.cpx = b.cpy = R(0);
+        // mirror reflection about grad v / |grad v| = (Im r, Re r) / |r|, in
+        // FP64 on the compensated momentum; for the grating r = 1/(1 + W0),
+        // so the normal is along (-Im W0, 1 + Re W0), formed from W0 itself
+        double nx, ny;
+        if constexpr (gauss_of(INTEG)) {
+            nx = (double)b.ri;
+            ny = (double)b.rr;
+        } else {
+            nx = -(double)b.wi;
+            ny = 1.0 + (double)b.wr;
+        }
+        const double il = 1.0 / sqrt(nx * nx + ny * ny);
+        nx *= il;
+        ny *= il;
+        const double vx = (double)b.px - (double)b.cpx, vy = (double)b.py - (double)b.cpy;
+        const double pn = vx * nx + vy * ny;
+        const double ox = vx - 2.0 * pn * nx, oy = vy - 2.0 * pn * ny;
+        b.px = (R)ox;
+        b.py = (R)oy;
+        b.cpx = (R)((double)b.px - ox);
+        b.cpy = (R)((double)b.py - oy);
         C.bounces++;
         surf = EV_GRATING;
         phase = PH_BOX;
@@ -1512,10 +1573,20 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     // (the time form converts its velocity to the momentum p = n^2 v first)
     R Nf[3];
     face_normal(ev_best, Nf);
+    // The momentum with its compensation term (the compensated sum carries
+    // the rounding of the FP32 sum: the exact sum is p - c); the time form's
+    // n^2 from W0 in FP64, as at the entry
     double n2f = 1.0;
-    if constexpr (integ_of(INTEG) == RT_RK4T)
-        n2f = ((double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri) / (double)k.is2;
-    const double p[3] = {(double)b.px * n2f, (double)b.py * n2f, (double)b.pz * n2f};
+    if constexpr (integ_of(INTEG) == RT_RK4T) {
+        if constexpr (gauss_of(INTEG)) {
+            n2f = ((double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri) / (double)k.is2;
+        } else {
+            const double ar = 1.0 + (double)b.wr, ai = (double)b.wi;
+            n2f = 1.0 / ((ar * ar + ai * ai) * (double)k.is2);
+        }
+    }
+    const double v[3] = {(double)b.px - (double)b.cpx, (double)b.py - (double)b.cpy, (double)b.pz};
+    const double p[3] = {v[0] * n2f, v[1] * n2f, v[2] * n2f};
     const double N[3] = {(double)Nf[0], (double)Nf[1], (double)Nf[2]};
     const double pn = p[0] * N[0] + p[1] * N[1] + p[2] * N[2];
     double pt[3];
@@ -1523,10 +1594,12 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     const double pt2 = pt[0] * pt[0] + pt[1] * pt[1] + pt[2] * pt[2];
     if (pt2 >= 1.0) {
         const double vn = pn / n2f;
-        b.px = (R)((double)b.px - 2.0 * vn * N[0]);
-        b.py = (R)((double)b.py - 2.0 * vn * N[1]);
-        b.pz = (R)((double)b.pz - 2.0 * vn * N[2]);
-        b.cpx = b.cpy = R(0);
+        const double vx = v[0] - 2.0 * vn * N[0], vy = v[1] - 2.0 * vn * N[1];
+        b.px = (R)vx;
+        b.py = (R)vy;
+        b.pz = (R)(v[2] - 2.0 * vn * N[2]);
+        b.cpx = (R)((double)b.px - vx);
+        b.cpy = (R)((double)b.py - vy);
         C.bounces++;
         surf = ev_best;
         phase = PH_BOX;
@@ -1556,9 +1629,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     }
     C.y = b.y;
     C.z = b.z;
-    C.dx = (R)(d[0] * il);
-    C.dy = (R)(d[1] * il);
-    C.dz = (R)(d[2] * il);
+    set_air_dir(C, d[0] * il, d[1] * il, d[2] * il);
     surf = EV_NONE;
     phase = PH_AIR;
 }
@@ -1733,9 +1804,7 @@ __device__ void start_branch(const DevScene& sc, Cold<R>& C, Box<R>& b, int& pha
         C.X = q.X;
         C.y = q.y;
         C.z = q.z;
-        C.dx = q.p[0];
-        C.dy = q.p[1];
-        C.dz = q.p[2];
+        set_air_dir_r(C, q.p[0], q.p[1], q.p[2]);
         C.in_plate = (q.medium == MED_PLATE);
         phase = PH_AIR;
     }

@@ -330,6 +330,8 @@ def run_gpu(args):
     fp32_cloak = {"cloak_ms": round(cl_ms, 3), "Mrays_per_s": round(cst["rays"] / (cl_ms * 1e-3) / 1e6, 3),
                   "Gsteps_per_s": round(cst["steps"] / (cl_ms * 1e-3) / 1e9, 4)}
 
+    accuracy = None if args.no_fp64 else fp32_accuracy(rt, torch, step, stream)
+
     # end to end through the C ABI, two frames in flight: every frame copies
     # its scene table in from pinned host memory, renders, computes C, and its
     # images and C are read back on a copy stream while the next frame renders
@@ -380,7 +382,15 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cpu = cpu_baseline(args.cpu_seconds)
+        def gpu_records(pix_np):
+            sc = step.scenes["cloak"]
+            pix = torch.tensor(pix_np, dtype=torch.int64, device="cuda")
+            rgb = torch.zeros((pix_np.size, 3), dtype=torch.float32, device="cuda")
+            rec = torch.zeros(pix_np.size * SPP * 80, dtype=torch.uint8, device="cuda")
+            sc.render_pixels(pix, rgb, rec, stream=stream)
+            torch.cuda.synchronize()
+            return rt.records_to_numpy(rec)
+        cpu = cpu_baseline(args.cpu_seconds, gpu_records)
 
     lat = {"p50_ms": round(float(np.percentile(step_ms, 50)), 3), "p99_ms": round(float(np.percentile(step_ms, 99)), 3)}
     line = {
@@ -395,6 +405,7 @@ def run_gpu(args):
         "frame_latency": lat,
         "fp32_cloak_render": fp32_cloak, "fp64_cloak_render": fp64,
         "fp32_over_fp64_steps": (round(fp32_cloak["Gsteps_per_s"] / fp64["Gsteps_per_s"], 2) if fp64 else None),
+        "fp32_accuracy": accuracy,
         "C": cvals,
         "roofline": roofline,
         "cpu_baseline": cpu,
@@ -415,6 +426,66 @@ def run_gpu(args):
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def record_errors(torch, rt, a_rec, b_rec) -> dict:
+    """Per-ray differences of two renders' exit records (same path = same
+    status and bounce count): the share within 1e-4 Lambda and 1e-5 rad on the
+    same path, and the largest and 99.9th-percentile position and direction
+    differences of the rays on the same path."""
+    a, b = rt.records_to_numpy(a_rec), rt.records_to_numpy(b_rec)
+    same = (a["status"] == b["status"]) & (a["bounces"] == b["bounces"])
+    dpos = np.abs(a["pos"] - b["pos"]).max(1)
+    ddir = np.linalg.norm(a["dir"] - b["dir"], axis=1)
+    ok = same & (dpos <= 1e-4) & (ddir <= 1e-5)
+    return {"rays": int(a.size), "within_tol": round(float(ok.mean()), 6), "same_path": round(float(same.mean()), 6),
+            "dpos_max": float(dpos[same].max()), "dpos_p999": float(np.percentile(dpos[same], 99.9)),
+            "ddir_max": float(ddir[same].max()), "ddir_p999": float(np.percentile(ddir[same], 99.9))}
+
+
+def fp32_accuracy(rt, torch, step, stream) -> dict:
+    """The FP32 results of the step against the FP64 path on the same inputs
+    (the FP64 path is held to the oracle within 1e-12 per ray by the parity
+    tests): per-ray exit errors of the cloaked and bare renders (all rays),
+    the share of pixels more than one 8-bit level apart in each of the six
+    renders, and |dC| of every C(0,0) the step reports.  Untimed."""
+    p64 = scenes_for(inputs.FP64)
+    out = {"reference": "FP64 GPU path (matches the oracle within 1e-12 per ray in the parity tests)",
+           "pixels_gt1_level": {}, "records": {}, "C_abs_diff": {}}
+    img64 = {}
+    for k in step.order:
+        s64 = rt.Scene(p64[k])
+        s32 = step.scenes[k]
+        img64[k] = torch.zeros(s64.shape, dtype=torch.float32, device="cuda")
+        q64 = torch.zeros(s64.shape, dtype=torch.uint8, device="cuda")
+        q32 = torch.zeros(s32.shape, dtype=torch.uint8, device="cuda")
+        i32 = torch.zeros(s32.shape, dtype=torch.float32, device="cuda")
+        recs = None
+        if k in ("cloak", "bare"):
+            n = s64.height * s64.wout * s64.spp * 80
+            recs = (torch.zeros(n, dtype=torch.uint8, device="cuda"), torch.zeros(n, dtype=torch.uint8, device="cuda"))
+        with torch.cuda.stream(stream):
+            s64.render(img64[k], q64, recs[0] if recs else None, stream=stream)
+            s32.render(i32, q32, recs[1] if recs else None, stream=stream)
+        torch.cuda.synchronize()
+        d = (q32.cpu().numpy().astype(int) - q64.cpu().numpy().astype(int))
+        out["pixels_gt1_level"][k] = float((np.abs(d).max(-1) > 1).mean())
+        if recs:
+            out["records"][k] = record_errors(torch, rt, recs[1], recs[0])
+        s64.close()
+    c32 = step.cvalues()
+    c_full = torch.zeros((2, 3, 4), dtype=torch.float64, device="cuda")
+    c_line = torch.zeros((2, 1, 4), dtype=torch.float64, device="cuda")
+    for q, g in enumerate(("cloak", "bare")):
+        rt.xcorr(img64["mirror"], img64[g], FOVS[1:], 50.0, out=c_full[q], stream=stream)
+        rt.xcorr(img64["mirror_line"], img64[g + "_line"], FOVS[:1], 50.0, out=c_line[q], stream=stream)
+    torch.cuda.synchronize()
+    f64, l64 = c_full.cpu().numpy(), c_line.cpu().numpy()
+    for q, g in enumerate(("cloak", "bare")):
+        ref = {"0": float(l64[q, 0, 3]), "10": float(f64[q, 0, 3]), "25": float(f64[q, 1, 3]), "50": float(f64[q, 2, 3])}
+        out["C_abs_diff"][f"C_{g}_vs_mirror"] = {fov: float(abs(c32[f"C_{g}_vs_mirror"][fov] - v))
+                                                 for fov, v in ref.items()}
+    return out
 
 
 def bench_xcorr_map(rt, torch, step, stream, clock_mhz: float) -> dict:
@@ -655,9 +726,11 @@ def bench_serving(rt, torch) -> dict:
     return out
 
 
-def cpu_baseline(seconds: float) -> dict:
+def cpu_baseline(seconds: float, gpu_records=None) -> dict:
     """The FP64 oracle as it stands, on the host cores, over a seeded pixel sample
-    of the cloaked-grating render (the dominant part of a step)."""
+    of the cloaked-grating render (the dominant part of a step).  With
+    `gpu_records` (pixel list -> the FP32 GPU path's records of those pixels)
+    the last sample is also compared with the GPU, ray by ray."""
     from oracle import oracle as orc
     orc.build()
     p = inputs.three_renders(inputs.config_main(precision=inputs.FP64))["cloak"]
@@ -669,16 +742,27 @@ def cpu_baseline(seconds: float) -> dict:
     while True:
         pix = inputs.pixel_subset(SIDE, SIDE, n, seed=99)
         t0 = time.perf_counter()
-        orc.render_pixels(sc, pix, nthreads=cores)
+        _, o_rec = orc.render_pixels(sc, pix, nthreads=cores, records=True)
         t = time.perf_counter() - t0
         total_rays += n * SPP
         total_t += t
         if total_t >= seconds or n >= SIDE * SIDE:
             break
         n = min(SIDE * SIDE, int(n * max(2.0, min(8.0, seconds / max(t, 1e-3) / 2))))
-    return {"value": round(total_rays / total_t / 1e6, 5), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
-            "sample": f"cloaked-grating render of the 512x512 4spp workload, seeded pixel subsets "
-                      f"(last {n} pixels), {total_rays} rays in {total_t:.1f} s"}
+    out = {"value": round(total_rays / total_t / 1e6, 5), "unit": "Mrays/s", "cores": cores, "kind": "oracle",
+           "sample": f"cloaked-grating render of the 512x512 4spp workload, seeded pixel subsets "
+                     f"(last {n} pixels), {total_rays} rays in {total_t:.1f} s"}
+    if gpu_records is not None:
+        g = gpu_records(pix).reshape(-1)
+        o = o_rec.reshape(-1)
+        same = (g["status"] == o["status"]) & (g["bounces"] == o["bounces"])
+        dpos = np.abs(g["pos"] - o["pos"]).max(1)
+        ddir = np.linalg.norm(g["dir"] - o["dir"], axis=1)
+        ok = same & (dpos <= 1e-4) & (ddir <= 1e-5)
+        out["fp32_vs_oracle"] = {"rays": int(o.size), "within_tol": round(float(ok.mean()), 6),
+                                 "dpos_max": float(dpos[same].max()), "ddir_max": float(ddir[same].max()),
+                                 "ddir_p999": float(np.percentile(ddir[same], 99.9))}
+    return out
 
 
 def run_reference(args):

@@ -132,6 +132,7 @@ def fp32_resolvable(orc, p, pix, spp, o_rec, tex=None):
 def compare_images(q_gpu, q_ref, max_frac=0.001):
     diff = np.abs(q_gpu.astype(int) - q_ref.astype(int)).max(-1)
     frac = (diff > 1).mean()
+    print({"pixels_gt1_level": float(frac), "pixels": int(diff.size)})
     assert frac <= max_frac, frac
     return frac
 
@@ -193,9 +194,8 @@ def test_render_small_config(rt, torch, orc, precision, kind):
     if precision == 1:
         info = compare_records(g["rec"], o_rec, min_frac=1.0)
     else:
-        cond = fp32_resolvable(orc, p, np.arange(64 * 64), 1, o_rec)
-        info = compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
-    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001 if kind != "cloak" else 0.002)
+        info = compare_records(g["rec"], o_rec, min_frac=0.999)
+    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001)
     assert g["stats"]["rays"] == 64 * 64
     if precision == 1:
         assert info["dpos_med"] < 1e-9
@@ -214,13 +214,29 @@ def test_render_main_config_sampled(rt, torch, orc, precision):
     if precision == 1:
         compare_records(grec, o_rec, min_frac=1.0)
     else:
+        # the bar over all rays, and over the rays the oracle finds well conditioned
         cond = fp32_resolvable(orc, p, pix, 4, o_rec)
-        compare_records(grec, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
+        compare_records(grec, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.999)
     q = g["rgb8"].reshape(-1, 3)[pix]
-    compare_images(q, orc.quantize(o_rgb), max_frac=0.002)
+    compare_images(q, orc.quantize(o_rgb), max_frac=0.001)
     st = g["stats"]
     assert st["rays"] == 512 * 512 * 4
     assert sum(st["status"]) == st["rays"]
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_render_main_config_all_rays(rt, torch, orc, precision):
+    """The full 512 x 512 x 4 cloaked render against the oracle on a seeded
+    quarter of its pixels (65536 pixels, 262144 rays): at least 99.9 % of all
+    rays within 1e-4 Lambda / 1e-5 rad on the same path (FP64: every ray), and
+    at most 0.1 % of those pixels more than one 8-bit level apart."""
+    p = inputs.three_renders(inputs.config_main(precision=precision))["cloak"]
+    g = gpu_render(rt, torch, p)
+    pix = inputs.pixel_subset(512, 512, 65536, seed=24)
+    o_rgb, o_rec = orc.render_pixels(orc.Scene(p), pix, records=True)
+    grec = g["rec"].reshape(512 * 512, 4)[pix]
+    compare_records(grec, o_rec, min_frac=1.0 if precision == 1 else 0.999)
+    compare_images(g["rgb8"].reshape(-1, 3)[pix], orc.quantize(o_rgb), max_frac=0.001)
 
 
 def test_render_pixels_equals_full_render(rt, torch, orc):
@@ -269,7 +285,7 @@ def test_edge_cases(rt, torch, orc, over, precision, variant):
         wout = 1 if p["centre_line"] else p["width"]
         cond = fp32_resolvable(orc, p, np.arange(p["height"] * wout), p["spp"], o_rec)
         compare_records(g["rec"], o_rec, pos_tol=POS_TOL * p["Lambda"], min_frac=1.0 - 1.0 / n, cond=cond,
-                        min_frac_all=0.97)
+                        min_frac_all=min(0.999, 1.0 - 1.0 / n))
     assert np.array_equal(np.sort(g["rec"]["status"].ravel()), np.sort(o_rec["status"].ravel())) or n > 100
 
 
@@ -289,8 +305,8 @@ def test_texture_background(rt, torch, orc):
     g = gpu_render(rt, torch, p, tex=tex)
     o_rgb, o_rec = orc.render(orc.Scene(p, tex=tex), records=True)
     cond = fp32_resolvable(orc, p, np.arange(30 * 40), 4, o_rec, tex)
-    compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
-    assert np.abs(g["rgb"] - o_rgb).max() < 0.05
+    compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.999)
+    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001)
     assert np.median(np.abs(g["rgb"] - o_rgb)) < 1e-5
 
 
@@ -316,20 +332,91 @@ def test_xcorr_parity(rt, torch, orc):
                 assert np.isnan(out[q]).all()
 
 
-def test_xcorr_of_renders(rt, torch, orc):
-    """C(cloak, mirror) and C(bare, mirror) of the small workload, GPU vs oracle,
-    within 1e-4."""
-    base = inputs.config_small(precision=0)
+C_TOL = 1e-4     # cross-correlations of renders, GPU against the oracle
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_xcorr_of_renders(rt, torch, orc, precision):
+    """C(cloak, mirror) and C(bare, mirror) of the small workload's renders
+    (64 x 64, one sample per pixel), GPU against the oracle, within 1e-4 at
+    FOV 0 (the centre-line renders), 10, 25 and 50 deg."""
+    base = inputs.config_small(precision=precision)
     imgs, refs = {}, {}
     for kind, p in inputs.three_renders(base).items():
-        imgs[kind] = torch.tensor(gpu_render(rt, torch, p, records=False)["rgb"], device="cuda")
-        refs[kind] = orc.render(orc.Scene(p))
+        for line in (0, 1):
+            q = dict(p, centre_line=line)
+            imgs[(kind, line)] = torch.tensor(gpu_render(rt, torch, q, records=False)["rgb"], device="cuda")
+            refs[(kind, line)] = orc.render(orc.Scene(q))
+    worst = 0.0
     for kind in ("cloak", "bare"):
-        out = rt.xcorr(imgs["mirror"], imgs[kind], [10.0, 25.0, 50.0], 50.0).cpu().numpy()
+        out = rt.xcorr(imgs[("mirror", 0)], imgs[(kind, 0)], [10.0, 25.0, 50.0], 50.0).cpu().numpy()
         for q, fov in enumerate([10.0, 25.0, 50.0]):
             j0, j1 = orc.fov_columns(64, 50.0, fov)
-            ref = orc.xcorr(refs["mirror"], refs[kind], j0, j1)
-            assert np.abs(out[q] - ref).max() < 1e-4 * 30, (kind, fov, out[q], ref)
+            ref = orc.xcorr(refs[("mirror", 0)], refs[(kind, 0)], j0, j1)
+            worst = max(worst, np.abs(out[q] - ref).max())
+            assert np.abs(out[q] - ref).max() < C_TOL, (kind, fov, out[q], ref)
+        out0 = rt.xcorr(imgs[("mirror", 1)], imgs[(kind, 1)], [0.0], 50.0).cpu().numpy()
+        ref0 = orc.xcorr(refs[("mirror", 1)], refs[(kind, 1)], 0, 1)
+        worst = max(worst, np.abs(out0[0] - ref0).max())
+        assert np.abs(out0[0] - ref0).max() < C_TOL, (kind, 0.0, out0[0], ref0)
+    print(f"precision {precision}: largest |dC| {worst:.2e}")
+
+
+def subset_columns(W, pix, j0, j1):
+    """Indices (into a pixel subset) of the pixels whose column lies in [j0, j1)."""
+    j = pix % W
+    return np.nonzero((j >= j0) & (j < j1))[0]
+
+
+_ORACLE_SUBSET = {}
+
+
+def oracle_subset(orc, p, pix):
+    """Oracle colours of a pixel subset (cached: the oracle traces in FP64
+    whatever precision the scene asks of the GPU)."""
+    key = (p["mirror"], p["cloak"], p.get("centre_line", 0), len(pix))
+    if key not in _ORACLE_SUBSET:
+        _ORACLE_SUBSET[key] = orc.render(orc.Scene(p)) if p.get("centre_line", 0) else \
+            orc.render_pixels(orc.Scene(p), pix)
+    return _ORACLE_SUBSET[key]
+
+
+@pytest.mark.parametrize("precision", [1, 0])
+def test_xcorr_of_benchmark_renders_sampled(rt, torch, orc, precision):
+    """The benchmark's 512 x 512 x 4 renders (mirror, bare and cloaked
+    grating) in full on the GPU, and a seeded subset of 65536 pixels of each
+    traced by the oracle.  Eq. 15 over the subset's pixels in each FOV window
+    (the window's columns restricted to the subset), packed into one column
+    per window and computed by rt_xcorr on the GPU renders and by the oracle
+    on its own: within 1e-4 at FOV 10, 25 and 50 deg; FOV 0 from the
+    centre-line renders in full."""
+    base = inputs.config_main(precision=precision)
+    pix = inputs.pixel_subset(512, 512, 65536, seed=23)
+    gimg, oimg = {}, {}
+    for kind, p in inputs.three_renders(base).items():
+        g = gpu_render(rt, torch, p, records=False)["rgb"].reshape(-1, 3)
+        gimg[kind] = g[pix]
+        oimg[kind] = oracle_subset(orc, p, pix)
+        q = dict(p, centre_line=1)
+        gimg[kind + "_line"] = gpu_render(rt, torch, q, records=False)["rgb"]
+        oimg[kind + "_line"] = oracle_subset(orc, q, pix)
+    worst = 0.0
+    for kind in ("cloak", "bare"):
+        for fov in (10.0, 25.0, 50.0):
+            j0, j1 = orc.fov_columns(512, 50.0, fov)
+            sel = subset_columns(512, pix, j0, j1)
+            f_g = torch.tensor(gimg["mirror"][sel][:, None, :], device="cuda")
+            g_g = torch.tensor(gimg[kind][sel][:, None, :], device="cuda")
+            got = rt.xcorr(f_g, g_g, [0.0], 50.0).cpu().numpy()[0]
+            ref = orc.xcorr(oimg["mirror"][sel][:, None, :], oimg[kind][sel][:, None, :], 0, 1)
+            worst = max(worst, np.abs(got - ref).max())
+            assert np.abs(got - ref).max() < C_TOL, (kind, fov, got, ref)
+        got0 = rt.xcorr(torch.tensor(gimg["mirror_line"], device="cuda"),
+                        torch.tensor(gimg[kind + "_line"], device="cuda"), [0.0], 50.0).cpu().numpy()[0]
+        ref0 = orc.xcorr(oimg["mirror_line"], oimg[kind + "_line"], 0, 1)
+        worst = max(worst, np.abs(got0 - ref0).max())
+        assert np.abs(got0 - ref0).max() < C_TOL, (kind, 0.0, got0, ref0)
+    print(f"precision {precision}: largest |dC| {worst:.2e}")
 
 
 # ---------------------------------------------------------------------------
@@ -352,8 +439,8 @@ def test_dp45_fp32_matches_oracle(rt, torch, orc, rtol):
     g = gpu_render(rt, torch, p)
     o_rgb, o_rec = orc.render(orc.Scene(p), records=True)
     cond = fp32_resolvable(orc, p, np.arange(64 * 64), 1, o_rec)
-    compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.98)
-    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.002)
+    compare_records(g["rec"], o_rec, min_frac=0.999, cond=cond, min_frac_all=0.999)
+    compare_images(g["rgb8"], orc.quantize(o_rgb), max_frac=0.001)
 
 
 @pytest.mark.parametrize("extent,A", [(2.0, 0.02), (8.0, 0.04), (32.0, 0.04)])
@@ -373,7 +460,7 @@ def test_hd_workload_sampled(rt, torch, orc, extent, A):
     g = rt.records_to_numpy(rec)
     o_rgb, o_rec = orc.render_pixels(orc.Scene(p, tex=tex), pix_np, records=True)
     cond = fp32_resolvable(orc, p, pix_np, 16, o_rec, tex)
-    compare_records(g, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.97)
+    compare_records(g, o_rec, min_frac=0.999, cond=cond, min_frac_all=0.995)
     assert np.median(np.abs(rgb.cpu().numpy() - o_rgb)) < 1e-4
 
 

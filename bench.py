@@ -569,7 +569,8 @@ def bench_hd(rt, torch, stream) -> dict:
     """The 1920 x 1080, 16 samples per pixel workload with adaptive
     Dormand-Prince (rtol = atol = 1e-5, FP32) and the seeded 2048^2
     value-noise background, over the cloak extents E = 2, 4, 8, 16, 32 Lambda
-    and amplitudes A = 0.02, 0.04: one full render each, timed."""
+    and amplitudes A = 0.02, 0.04: one full render each, timed after an
+    untimed warm-up render of the same scene."""
     tex = inputs.value_noise(2048, seed=3)
     out = {}
     total_rays, total_ms, total_steps = 0, 0.0, 0
@@ -577,6 +578,9 @@ def bench_hd(rt, torch, stream) -> dict:
         for E in (2.0, 4.0, 8.0, 16.0, 32.0):
             sc = rt.Scene(inputs.config_hd(extent=E, A=A, precision=inputs.FP32), tex=tex)
             img = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
+            with torch.cuda.stream(stream):
+                sc.render(img, stream=stream)           # warm-up: the scene's first launch is not timed
+            torch.cuda.synchronize()
             with torch.cuda.stream(stream):
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
@@ -690,39 +694,62 @@ def bench_batch(rt, torch, stream) -> dict:
             "Gsteps_per_s": round(st["steps"] / ms / 1e6, 3), "min_active": m, "autotune_s": round(tune_s, 2)}
 
 
-def bench_serving(rt, torch) -> dict:
-    """Poisson arrivals of render requests (seed 5; side log-uniform in
-    [256, 2048], spp log-uniform in [1, 64]; scenes as in the batch workload)
-    served under a 40 GB ray-state budget: once at the offered 200 requests/s
-    (far above capacity: the queue builds, latency is the saturation value),
-    once at a rate the GPU sustains.  Latency is submission to completion."""
-    out = {}
-    for label, rate, count in (("offered_200_per_s", 200.0, 24), ("sustained", 2.0, 16)):
-        reqs = inputs.serving_requests(count, seed=5, rate=rate, precision=inputs.FP32)
-        imgs = [torch.zeros((p["height"], p["width"], 3), dtype=torch.float32, device="cuda") for _, p in reqs]
-        server = rt.Server(budget_bytes=40 * 10**9, max_inflight=4)
-        tickets = []
-        t0 = time.perf_counter()
-        for (t_arr, p), img in zip(reqs, imgs):
-            while time.perf_counter() - t0 < t_arr:
-                time.sleep(0.0002)
-            tickets.append(server.submit(p, img))
-        res = {}
-        while len(res) < len(tickets) and time.perf_counter() - t0 < 600:
+def serve_leg(rt, torch, rate: float, count: int, seed: int = 5) -> dict:
+    """Serve `count` requests arriving as a Poisson process of mean rate `rate`
+    (seed `seed`; side log-uniform in [256, 2048], spp log-uniform in [1, 64],
+    scenes as in the batch workload) under a 40 GB ray-state budget; latency is
+    submission to completion."""
+    reqs = inputs.serving_requests(count, seed=seed, rate=rate, precision=inputs.FP32)
+    imgs = [torch.zeros((p["height"], p["width"], 3), dtype=torch.float32, device="cuda") for _, p in reqs]
+    server = rt.Server(budget_bytes=40 * 10**9, max_inflight=2)
+    tickets, res, max_queued = [], {}, 0
+    t0 = time.perf_counter()
+    for (t_arr, p), img in zip(reqs, imgs):
+        while time.perf_counter() - t0 < t_arr:
             for t in tickets:
                 if t not in res:
-                    r = server.poll(t, timeout_us=1000)
+                    r = server.poll(t, timeout_us=0)
                     if r is not None:
                         res[t] = r
-        wall = time.perf_counter() - t0
-        server.close()
-        lat = np.array([r["latency_ms"] for r in res.values()])
-        rays = sum(r["rays"] for r in res.values())
-        out[label] = {"requests": len(reqs), "completed": len(res), "arrival_rate_per_s": rate,
-                      "p50_ms": round(float(np.percentile(lat, 50)), 2), "p99_ms": round(float(np.percentile(lat, 99)), 2),
-                      "Mrays_per_s": round(rays / wall / 1e6, 3), "wall_s": round(wall, 2)}
-        del imgs
-        torch.cuda.empty_cache()
+            time.sleep(0.0002)
+        tickets.append(server.submit(p, img))
+        max_queued = max(max_queued, server.stats()["queued"])
+    while len(res) < len(tickets) and time.perf_counter() - t0 < 900:
+        for t in tickets:
+            if t not in res:
+                r = server.poll(t, timeout_us=500)
+                if r is not None:
+                    res[t] = r
+        max_queued = max(max_queued, server.stats()["queued"])
+    wall = time.perf_counter() - t0
+    server.close()
+    lat = np.array([r["latency_ms"] for r in res.values()])
+    rays = sum(r["rays"] for r in res.values())
+    p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
+    out = {"requests": len(reqs), "completed": len(res), "failed": sum(r["status"] != 0 for r in res.values()),
+           "arrival_rate_per_s": round(rate, 3), "p50_ms": round(p50, 2), "p99_ms": round(p99, 2),
+           "p99_over_p50": round(p99 / p50, 2), "mean_ms": round(float(lat.mean()), 2),
+           "Mrays_per_s": round(rays / wall / 1e6, 3), "wall_s": round(wall, 2), "max_queued": max_queued,
+           "mean_rays_per_request": round(rays / max(len(res), 1))}
+    del imgs
+    torch.cuda.empty_cache()
+    return out
+
+
+def bench_serving(rt, torch) -> dict:
+    """Config 5: Poisson arrivals of render requests served from the
+    device-resident request ring.  First the offered 200 requests/s (far
+    above capacity: the queue builds, latency is the saturation value, and
+    the GPU is busy throughout, so the leg measures the service capacity);
+    then the highest sustainable rate for this request mix, the capacity in
+    requests/s (throughput / mean rays per request), and a leg at 80 % of it,
+    whose queue stays bounded."""
+    out = {}
+    sat = serve_leg(rt, torch, rate=200.0, count=200)
+    out["offered_200_per_s"] = sat
+    capacity = sat["Mrays_per_s"] * 1e6 / sat["mean_rays_per_request"]
+    out["max_sustainable_req_per_s"] = round(capacity, 2)
+    out["load_80_percent"] = serve_leg(rt, torch, rate=0.8 * capacity, count=200)
     return out
 
 

@@ -330,20 +330,27 @@ int rt_validate_desc(const rt_scene_desc* desc);
  * requests in arrival order while the sum of their ray-state footprints
  * (76 bytes per sample: 64 of ray state and a 12-byte colour slot; 16 bytes
  * per pixel: the float output image and a sample counter; see
- * rt_request_bytes) stays within the budget,
- * groups the newly admitted requests that share precision and integrator
- * into one batch launch and runs it on a free stream (at most max_inflight
- * batches in flight).  Requests that arrive while batches run are admitted as
- * budget and streams free up; their work overlaps on the device.  Each
- * result equals a render of the scene alone.  Device allocations of a batch
- * are stream-ordered on its stream.
+ * rt_request_bytes) stays within the budget, and publishes each admitted
+ * request into a ring of request slots in device memory (one ring per
+ * precision and integrator, 1024 requests in flight each).  A persistent
+ * launch of the wavefront loop takes samples from the ring up to the
+ * published count: requests published while it runs are taken up as its
+ * lanes free up, so their work overlaps on the device with the requests
+ * already running, and a small request does not wait for a large one to end.
+ * A launch ends when no sample is left; at most max_inflight launches run at
+ * once.  The last pixel of a request writes a completion record into
+ * host-mapped memory.  Each result equals a render of the scene alone.
+ * Scratch and textures of the requests in flight come from a device arena
+ * allocated with the server (at most the budget, at most half of the free
+ * device memory); nothing is allocated per request.  Scenes with options
+ * (RT_FLAG_*) and the Gaussian bump are not served.
  */
 typedef struct rt_server rt_server;
 
 typedef struct rt_result {
     int32_t status;           /* RT_OK or the error of the request           */
     float latency_ms;         /* submission to completion                     */
-    float queue_ms;           /* submission to launch                         */
+    float queue_ms;           /* submission to publication on the device       */
     uint64_t rays;            /* camera samples of the request                */
 } rt_result;
 
@@ -357,11 +364,12 @@ typedef struct rt_server_info {
    invalid descriptor. */
 int rt_request_bytes(const rt_scene_desc* desc, uint64_t* bytes);
 
-/* rt_server_create: server on the current device; max_inflight 1..16. */
+/* rt_server_create: server on the current device; max_inflight 1..16 launches
+   of the server kernel per ring; RT_ENOMEM if the arena cannot be allocated. */
 int rt_server_create(size_t ray_state_budget_bytes, int32_t max_inflight, rt_server** out);
 
 /* rt_server_destroy: fails the requests not yet admitted (RT_ETIMEDOUT),
-   waits for the batches in flight, stops the worker. */
+   finishes the requests in flight, stops the worker. */
 void rt_server_destroy(rt_server* server);
 
 /* rt_submit: queue a request rendering into d_out (caller-owned device image

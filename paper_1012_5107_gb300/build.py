@@ -20,6 +20,9 @@ SOURCES = ["rt_api.cu", "rt_render.cu", "rt_batch.cu", "rt_server.cu", "rt_xcorr
            "rt_xcorr_map.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC]
+# The render server's kernels read request slots that the host rewrites while
+# they run: their global loads are cached in L2 only (no stale L1 lines).
+FILE_FLAGS = {"rt_server.cu": ["-Xptxas", "-dlcm=cg"]}
 
 
 def nvcc() -> str:
@@ -46,7 +49,7 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc(), *ARCH, *FLAGS, *FILE_FLAGS.get(src, []), "-c", s, "-o", o]
             if ptxas_info:
                 cmd += ["-Xptxas", "-v"]
             if verbose:

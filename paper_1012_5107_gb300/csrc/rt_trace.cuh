@@ -36,6 +36,13 @@
 #include "rt_gauss.cuh"
 #include "rt_internal.h"
 
+// Texel loads of the background.  A launch whose textures stay put reads
+// them through the read-only data cache; the render server, whose running
+// launches meet textures copied in while they run, loads them from L2.
+#ifndef RT_TEX_LOAD
+#define RT_TEX_LOAD __ldg
+#endif
+
 namespace grt {
 
 // The integrator template argument INTEG of the tracer also carries the
@@ -108,6 +115,21 @@ __device__ __forceinline__ void set_air_dir(Cold<R>& C, double x, double y, doub
     C.dl[0] = (float)(x - (double)C.dx);
     C.dl[1] = (float)(y - (double)C.dy);
     C.dl[2] = (float)(z - (double)C.dz);
+}
+
+// The residual matters only where a box face lies ahead (Snell's law); scenes
+// without a cloak box or plate skip its FP64 work.
+template <class R>
+__device__ __forceinline__ void set_air_dir_if(Cold<R>& C, bool keep, double x, double y, double z)
+{
+    if (keep) {
+        set_air_dir(C, x, y, z);
+    } else {
+        C.dx = (R)x;
+        C.dy = (R)y;
+        C.dz = (R)z;
+        C.dl[0] = C.dl[1] = C.dl[2] = 0.0f;
+    }
 }
 
 // A direction known only in the path's precision (no residual).
@@ -984,7 +1006,7 @@ __device__ __forceinline__ void camera_start(const DevScene& sc, Cold<R>& C)
     C.X = (R)(Px - cxd);
     C.y = (R)(sc.C[1] + t * d[1]);
     C.z = (R)(sc.C[2] + t * d[2]);
-    set_air_dir(C, d[0], d[1], d[2]);
+    set_air_dir_if(C, sc.cloak || (opt_flags<OPT>(sc) & RT_FLAG_PLATE), d[0], d[1], d[2]);
 }
 
 // Straight line against the flat mirror y = 0.
@@ -1226,8 +1248,8 @@ __device__ __forceinline__ int background(const DevScene& sc, const AirConst<R>&
         if (u0 < 0) u0 += N;
         if (v0 < 0) v0 += N;
         const long long u1 = (u0 + 1 == N) ? 0 : u0 + 1, v1 = (v0 + 1 == N) ? 0 : v0 + 1;
-        const float t00 = __ldg(sc.tex + v0 * N + u0), t01 = __ldg(sc.tex + v0 * N + u1);
-        const float t10 = __ldg(sc.tex + v1 * N + u0), t11 = __ldg(sc.tex + v1 * N + u1);
+        const float t00 = RT_TEX_LOAD(sc.tex + v0 * N + u0), t01 = RT_TEX_LOAD(sc.tex + v0 * N + u1);
+        const float t10 = RT_TEX_LOAD(sc.tex + v1 * N + u0), t11 = RT_TEX_LOAD(sc.tex + v1 * N + u1);
         const float val = (1.0f - fu) * (1.0f - fv) * t00 + fu * (1.0f - fv) * t01 + (1.0f - fu) * fv * t10 +
                           fu * fv * t11;
         col[0] = col[1] = col[2] = val;
@@ -1478,7 +1500,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                 double d[3];
                 air_dir(C, d);
                 const double pn = (d[0] * nx + d[1] * ny) * il;
-                set_air_dir(C, d[0] - 2.0 * pn * nx * il, d[1] - 2.0 * pn * ny * il, d[2]);
+                set_air_dir_if(C, sc.cloak || plate, d[0] - 2.0 * pn * nx * il, d[1] - 2.0 * pn * ny * il, d[2]);
             } else {
                 advance(C, tm);
                 C.y = R(0);
@@ -1851,6 +1873,21 @@ struct OneScene {
     }
     __device__ __forceinline__ int64_t sample_slot(int, int64_t out, int sample) const { return out * sc.spp + sample; }
     __device__ __forceinline__ int64_t pixel_slot(int, int64_t out) const { return out; }
+    // colour slot of sample `sample` of output pixel `out`, and the pixel's counter
+    __device__ __forceinline__ float* sample_col(int s, int64_t out, int sample) const
+    {
+        return samp_col + 3 * sample_slot(s, out, sample);
+    }
+    __device__ __forceinline__ int* pixel_count(int s, int64_t out) const { return pix_cnt + pixel_slot(s, out); }
+    // the next work items of the calling lanes (warp-aggregated); -1 when none is left
+    __device__ __forceinline__ int64_t grab(unsigned long long* counters, unsigned lane) const
+    {
+        const int64_t ws = grab_work(&counters[0], lane);
+        return ws < nsamples() ? ws : -1;
+    }
+    __device__ __forceinline__ void pixel_done(int) const {}
+    // the launch's counters are cleared before it starts: nothing to do
+    __device__ __forceinline__ void release_count(int, int64_t) const {}
     __device__ __forceinline__ float* rgb_of(int) const { return rgb; }
     __device__ __forceinline__ uint8_t* rgb8_of(int) const { return rgb8; }
     __device__ __forceinline__ rt_ray_record* rec_of(int) const { return rec; }
@@ -1900,6 +1937,18 @@ struct ManyScenes {
         return __ldg(soffsets + s) + out * scenes[s].spp + sample;
     }
     __device__ __forceinline__ int64_t pixel_slot(int s, int64_t out) const { return __ldg(offsets + s) + out; }
+    __device__ __forceinline__ float* sample_col(int s, int64_t out, int sample) const
+    {
+        return samp_col + 3 * sample_slot(s, out, sample);
+    }
+    __device__ __forceinline__ int* pixel_count(int s, int64_t out) const { return pix_cnt + pixel_slot(s, out); }
+    __device__ __forceinline__ int64_t grab(unsigned long long* counters, unsigned lane) const
+    {
+        const int64_t ws = grab_work(&counters[0], lane);
+        return ws < nsamples() ? ws : -1;
+    }
+    __device__ __forceinline__ void pixel_done(int) const {}
+    __device__ __forceinline__ void release_count(int, int64_t) const {}
     __device__ __forceinline__ float* rgb_of(int s) const { return rgbs[s]; }
     __device__ __forceinline__ uint8_t* rgb8_of(int) const { return nullptr; }
     __device__ __forceinline__ rt_ray_record* rec_of(int) const { return nullptr; }

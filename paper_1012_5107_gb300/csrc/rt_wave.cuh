@@ -144,18 +144,18 @@ __device__ __forceinline__ void wave_finish_sample(const Src& src, const DevScen
     float acc[3] = {C.acc[0], C.acc[1], C.acc[2]};
     const int spp = sc.spp;
     if (spp > 1) {
-        const int64_t gs = src.sample_slot(C.scene, C.work, C.sample);
-        float* col = src.samp_col + 3 * gs;
+        float* col = src.sample_col(C.scene, C.work, C.sample);
         col[0] = acc[0];
         col[1] = acc[1];
         col[2] = acc[2];
         __threadfence();                                     // the colour before the count
-        if (atomicAdd(src.pix_cnt + src.pixel_slot(C.scene, C.work), 1) != spp - 1) return;
+        if (atomicAdd(src.pixel_count(C.scene, C.work), 1) != spp - 1) return;
         __threadfence();                                     // the count before the other colours
-        const float* base = src.samp_col + 3 * (gs - C.sample);
+        const float* base = col - 3 * C.sample;
         acc[0] = acc[1] = acc[2] = 0.0f;
         for (int q = 0; q < spp; ++q)
             for (int a = 0; a < 3; ++a) acc[a] += __ldcg(base + 3 * q + a);
+        src.release_count(C.scene, C.work);
     }
     const float inv = 1.0f / (float)spp;
     float c[3];
@@ -167,6 +167,7 @@ __device__ __forceinline__ void wave_finish_sample(const Src& src, const DevScen
         uint8_t* q = q8 + 3 * C.work;
         q[0] = quantize8(c[0]); q[1] = quantize8(c[1]); q[2] = quantize8(c[2]);
     }
+    src.pixel_done(C.scene);
 }
 
 template <class R, int INTEG, bool OPT, class Src>
@@ -201,7 +202,6 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
     __syncthreads();
 
     const unsigned lane = threadIdx.x & 31u;
-    const int64_t nsamples = src.nsamples();
     LaneStats st = {0u, 0u, 0u, 0u};
 #if RT_PROFILE
     // per warp (lane 0): cycles in integration tasks, cycles in service
@@ -325,8 +325,8 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                     if (phase == PH_EVENT || phase == PH_GUARD)
                         service_event<R, INTEG, OPT>(src.scene(C.scene), C, b, phase, surf, steps, src.rec_of(C.scene), st);
                     if (phase == PH_IDLE) {
-                        const int64_t ws = grab_work(&counters[0], lane);
-                        if (ws >= nsamples) { phase = PH_EXIT; break; }
+                        const int64_t ws = src.grab(counters, lane);
+                        if (ws < 0) { phase = PH_EXIT; break; }
                         int s, sample;
                         int64_t pix, out;
                         src.map_sample(ws, s, pix, out, sample);

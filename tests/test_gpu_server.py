@@ -1,6 +1,7 @@
-"""The render server: continuous batching under a ray-state budget.  Every
-result equals a render of the same scene alone (the scenes are mixed into
-shared batch launches and overlap on the device)."""
+"""The render server: continuous batching under a ray-state budget, with
+the requests in a device-resident ring that a running launch takes work
+from.  Every result equals a render of the same scene alone (the scenes are
+mixed into shared launches and overlap on the device)."""
 import time
 
 import numpy as np
@@ -126,3 +127,57 @@ def test_close_with_work_pending(rt):
         server.submit(p, o)
     server.close()                               # waits for flights, fails the rest
     torch.cuda.synchronize()
+
+
+def test_running_launch_takes_new_requests(rt):
+    """A small request submitted while a large one is on the GPU finishes
+    first: the running launch takes its samples as lanes free up, instead of
+    the request waiting for the large one to end."""
+    import torch
+    big = inputs.base_scene(width=1024, height=1024, spp=16, seed=21, scene_id=1, precision=0)
+    small = inputs.base_scene(width=48, height=40, spp=4, seed=22, scene_id=2, precision=0)
+    ref = torch.zeros((40, 48, 3), dtype=torch.float32, device="cuda")
+    sc = rt.Scene(small)
+    sc.render(ref)
+    torch.cuda.synchronize()
+    server = rt.Server(budget_bytes=4 << 30, max_inflight=2)
+    out_big = torch.zeros((1024, 1024, 3), dtype=torch.float32, device="cuda")
+    out_small = torch.full((40, 48, 3), -1.0, dtype=torch.float32, device="cuda")
+    tb = server.submit(big, out_big)
+    time.sleep(0.01)                                    # the large request is running
+    ts = server.submit(small, out_small)
+    rs = None
+    for _ in range(20000):
+        rs = server.poll(ts, timeout_us=1000)
+        if rs is not None:
+            break
+    assert rs is not None and rs["status"] == 0
+    assert server.poll(tb) is None                      # the large one is still running
+    rb = wait_all(server, [tb])[tb]
+    assert rb["status"] == 0 and rb["latency_ms"] > rs["latency_ms"] + 10.0
+    torch.cuda.synchronize()
+    assert torch.equal(out_small, ref)
+    server.close()
+
+
+def test_ring_wraps_around(rt):
+    """More requests than the ring has slots (1024), each equal to its render alone."""
+    import torch
+    n = 1100
+    ps = [inputs.base_scene(width=8, height=6, spp=1 + (q % 3), seed=100 + q, scene_id=q, precision=0)
+          for q in range(n)]
+    server = rt.Server(budget_bytes=1 << 28, max_inflight=2)
+    outs = [torch.zeros((6, 8, 3), dtype=torch.float32, device="cuda") for _ in ps]
+    tickets = [server.submit(p, o) for p, o in zip(ps, outs)]
+    res = wait_all(server, tickets, limit_s=300.0)
+    assert len(res) == n and all(r["status"] == 0 for r in res.values())
+    torch.cuda.synchronize()
+    for q in (0, 1, 513, 1023, 1024, 1025, n - 1):
+        sc = rt.Scene(ps[q])
+        ref = torch.zeros((6, 8, 3), dtype=torch.float32, device="cuda")
+        sc.render(ref)
+        torch.cuda.synchronize()
+        assert torch.equal(outs[q], ref), q
+    st = server.stats()
+    assert st["completed"] == n and st["in_flight"] == 0 and st["bytes_in_use"] == 0
+    server.close()

@@ -378,7 +378,7 @@ static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float
             s->d_samp = nullptr;
             s->d_pcnt = nullptr;
             s->samp_cap = s->pix_cap = 0;
-            RT_CK(cudaMallocAsync((void**)&s->d_samp, (size_t)ns * kScratchBytesPerSample, st));
+            RT_CK(cudaMallocAsync((void**)&s->d_samp, (size_t)nwork * (size_t)col_block_bytes(sc.spp), st));
             RT_CK(cudaMallocAsync((void**)&s->d_pcnt, (size_t)nwork * kScratchBytesPerPixel, st));
             s->samp_cap = ns;
             s->pix_cap = nwork;

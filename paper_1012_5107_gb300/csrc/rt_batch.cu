@@ -225,10 +225,13 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
         if (x.mirror != y.mirror) return x.mirror > y.mirror;
         return x.nwork * x.spp < y.nwork * y.spp;
     });
+    int64_t cols = 0;                         // floats of pixel colour blocks
     for (int j = 0; j < n; ++j) {
         dev[j] = user[order[j]];
         off[j + 1] = off[j] + dev[j].nwork;
         soff[j + 1] = soff[j] + dev[j].nwork * dev[j].spp;
+        dev[j].col_base = cols;
+        if (dev[j].spp > 1) cols += dev[j].nwork * (col_block_bytes(dev[j].spp) >> 2);
     }
     int cur = -1;
     RT_CK(cudaGetDevice(&cur));
@@ -248,7 +251,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     cudaError_t e = cudaMalloc(&b->d_scenes, sizeof(DevScene) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_offsets, sizeof(int64_t) * (n + 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_soffsets, sizeof(int64_t) * (n + 1));
-    if (e == cudaSuccess) e = cudaMalloc(&b->d_samp, kScratchBytesPerSample * (size_t)b->total_samples);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_samp, sizeof(float) * (size_t)(cols > 0 ? cols : 1));
     if (e == cudaSuccess) e = cudaMalloc(&b->d_pcnt, kScratchBytesPerPixel * (size_t)b->total);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_rgbs, sizeof(float*) * n);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counters, sizeof(unsigned long long) * kCounters);
@@ -321,6 +324,7 @@ int rt_batch_update(rt_batch* b, const rt_scene_desc* descs, int32_t n, void* st
         dev[j].tex = old.tex;
         dev[j].tex_size = old.tex_size;
         dev[j].pix_list = nullptr;
+        dev[j].col_base = old.col_base;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t bytes = sizeof(DevScene) * (size_t)n;

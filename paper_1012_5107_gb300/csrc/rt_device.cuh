@@ -71,6 +71,7 @@ struct DevScene {
     uint64_t seed, scene_id;
     int64_t max_steps;
     int64_t nwork;                          // pixels to render
+    int64_t col_base;                       // first float of the scene's pixel colour blocks in the launch scratch
     int mirror, cloak, width, height, wout, spp, m, centre_line;
     int background, tex_size, integrator, max_bounces;
     int flags;                              // RT_FLAG_*
@@ -135,6 +136,31 @@ template <> struct Mth<double> {
     static constexpr double kRehit = 1e-9;
     static constexpr double kEps = 2.220446049250313e-16;
 };
+
+// FP64 reciprocal and reciprocal square root for the few FP64 steps of the
+// FP32 path (interfaces, reflections): an FP32 seed from the SFU refined by
+// two Newton-Raphson steps in FP64 -- y <- y (2 - x y) and
+// y <- y (3 - x y^2) / 2, each squaring the relative error (2^-23 -> 2^-46
+// -> below the FP64 rounding) -- instead of a full-precision FP64 division
+// or square root, which take many more operations on the FP64 pipe.
+// Arguments are positive and within the FP32 range.
+__device__ __forceinline__ double recip_nr(double x)
+{
+    float s;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(s) : "f"((float)x));
+    double y = (double)s;
+    y = y * fma(-x, y, 2.0);
+    y = y * fma(-x, y, 2.0);
+    return y;
+}
+
+__device__ __forceinline__ double rsqrt_nr(double x)
+{
+    double y = (double)rsqrtf((float)x);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    y = y * fma(-0.5 * x * y, y, 1.5);
+    return y;
+}
 
 // ------------------------------------------------------------------------
 // Packed FP32 pairs: sm_100 and later issue two FP32 fused multiply-adds,

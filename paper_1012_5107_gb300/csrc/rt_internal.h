@@ -56,6 +56,11 @@ struct SampleScratch {
 size_t branch_queue_bytes(int precision, int grid);
 constexpr size_t kScratchBytesPerSample = 3 * sizeof(float);
 constexpr size_t kScratchBytesPerPixel = sizeof(int);
+// The colours of a pixel's samples sit in one block of whole 128-byte L2
+// lines, 16 bytes a sample (three floats and a pad, so that every 32-byte
+// sector is written in full): once the pixel's last sample has summed them,
+// the lines are discarded from L2 without being written back to DRAM.
+__host__ __device__ constexpr int64_t col_block_bytes(int spp) { return ((int64_t)spp * 16 + 127) / 128 * 128; }
 
 // Bounds of the wavefront loop's waits on its work queues: attempts per wait
 // and whether every block starts with its queue lock held (rt_scene_set_wait_limit).

@@ -58,7 +58,7 @@ constexpr int kRingKinds = 6;             // precision x integrator (RK4, DP45, 
 struct RingSlot {
     DevScene sc;                 // its scene table (nwork = pixels)
     float* out;                  // caller's image
-    float* samp;                 // 3 floats per sample (spp > 1)
+    float* samp;                 // the pixels' colour blocks (col_block_bytes each; spp > 1)
     int* pcnt;                   // one counter per pixel (spp > 1), zero at publication and after
     long long nsamples;
     long long npix;
@@ -175,7 +175,7 @@ struct RingScenes {
     }
     __device__ __forceinline__ float* sample_col(int s, int64_t out, int sample) const
     {
-        return slots[s].samp + 3 * (out * slots[s].sc.spp + sample);
+        return slots[s].samp + (col_block_bytes(slots[s].sc.spp) >> 2) * out + 4 * sample;
     }
     __device__ __forceinline__ int* pixel_count(int s, int64_t out) const { return slots[s].pcnt + out; }
     // The pixel's last sample sets its counter back to zero: the counters
@@ -488,7 +488,7 @@ static cudaError_t publish(rt_server* S, Ring& g, Request& r)
     cudaError_t e = cudaSuccess;
     if (h.sc.spp > 1) {
         h.samp = (float*)(base + at);
-        at += align_up(kScratchBytesPerSample * (size_t)ns);
+        at += align_up((size_t)col_block_bytes(h.sc.spp) * (size_t)npix);
         h.pcnt = (int*)(S->counters.base + r.cnt_off);
     }
     if (e == cudaSuccess && !r.tex.empty()) {
@@ -627,7 +627,7 @@ static void worker_main(rt_server* S)
             const size_t npix = (size_t)d.height * (d.centre_line ? 1 : (size_t)d.width);
             size_t need = 0, need_cnt = 0;
             if (d.spp > 1) {
-                need += align_up(kScratchBytesPerSample * npix * d.spp);
+                need += align_up((size_t)col_block_bytes(d.spp) * npix);
                 need_cnt = align_up(kScratchBytesPerPixel * npix);
             }
             need += align_up(r.tex.size() * sizeof(float));

@@ -1445,7 +1445,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                 n2 = (double)b.rr * (double)b.rr + (double)b.ri * (double)b.ri;
             } else {
                 const double ar = 1.0 + (double)b.wr, ai = (double)b.wi;
-                n2 = 1.0 / (ar * ar + ai * ai);
+                n2 = recip_nr(ar * ar + ai * ai);
             }
             if (opt_flags<OPT>(sc) & RT_FLAG_REFERENCED) n2 *= sc.idx_scale * sc.idx_scale;
             if (n2 < pt2) {      // total reflection off the outside of the box
@@ -1570,7 +1570,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
             nx = -(double)b.wi;
             ny = 1.0 + (double)b.wr;
         }
-        const double il = 1.0 / sqrt(nx * nx + ny * ny);
+        const double il = rsqrt_nr(nx * nx + ny * ny);
         nx *= il;
         ny *= il;
         const double vx = (double)b.px - (double)b.cpx, vy = (double)b.py - (double)b.cpy;
@@ -1844,9 +1844,10 @@ __device__ __forceinline__ uint8_t quantize8(float c)
 // other (constants in device memory).
 // Pixels are numbered by work item (w), samples by w * spp + sample; the
 // wavefront loop takes samples as its work items, the per-lane loop pixels.
-// Samples of one pixel traced by different lanes leave their colours in
-// samp_col (3 floats per sample) and count themselves in pix_cnt (one int per
-// pixel, zero at launch); the last one sums them in sample order.
+// Samples of one pixel traced by different lanes leave their colours in the
+// pixel's block of samp_col (col_block_bytes, from the scene's col_base on)
+// and count themselves in pix_cnt (one int per pixel, zero at launch); the
+// last one sums them in sample order.
 struct OneScene {
     static constexpr bool kParamScene = true;    // the scene lives in the kernel parameters
     const DevScene& sc;
@@ -1876,7 +1877,7 @@ struct OneScene {
     // colour slot of sample `sample` of output pixel `out`, and the pixel's counter
     __device__ __forceinline__ float* sample_col(int s, int64_t out, int sample) const
     {
-        return samp_col + 3 * sample_slot(s, out, sample);
+        return samp_col + scene(s).col_base + (col_block_bytes(scene(s).spp) >> 2) * out + 4 * sample;
     }
     __device__ __forceinline__ int* pixel_count(int s, int64_t out) const { return pix_cnt + pixel_slot(s, out); }
     // the next work items of the calling lanes (warp-aggregated); -1 when none is left
@@ -1939,7 +1940,7 @@ struct ManyScenes {
     __device__ __forceinline__ int64_t pixel_slot(int s, int64_t out) const { return __ldg(offsets + s) + out; }
     __device__ __forceinline__ float* sample_col(int s, int64_t out, int sample) const
     {
-        return samp_col + 3 * sample_slot(s, out, sample);
+        return samp_col + scene(s).col_base + (col_block_bytes(scene(s).spp) >> 2) * out + 4 * sample;
     }
     __device__ __forceinline__ int* pixel_count(int s, int64_t out) const { return pix_cnt + pixel_slot(s, out); }
     __device__ __forceinline__ int64_t grab(unsigned long long* counters, unsigned lane) const

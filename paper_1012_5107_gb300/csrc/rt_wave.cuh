@@ -145,17 +145,23 @@ __device__ __forceinline__ void wave_finish_sample(const Src& src, const DevScen
     const int spp = sc.spp;
     if (spp > 1) {
         float* col = src.sample_col(C.scene, C.work, C.sample);
-        col[0] = acc[0];
-        col[1] = acc[1];
-        col[2] = acc[2];
+        __stcg(reinterpret_cast<float4*>(col), make_float4(acc[0], acc[1], acc[2], 0.0f));
         __threadfence();                                     // the colour before the count
         if (atomicAdd(src.pixel_count(C.scene, C.work), 1) != spp - 1) return;
         __threadfence();                                     // the count before the other colours
-        const float* base = col - 3 * C.sample;
+        const float4* base = reinterpret_cast<const float4*>(col) - C.sample;
         acc[0] = acc[1] = acc[2] = 0.0f;
-        for (int q = 0; q < spp; ++q)
-            for (int a = 0; a < 3; ++a) acc[a] += __ldcg(base + 3 * q + a);
+        for (int q = 0; q < spp; ++q) {
+            const float4 v = __ldcg(base + q);
+            acc[0] += v.x;
+            acc[1] += v.y;
+            acc[2] += v.z;
+        }
         src.release_count(C.scene, C.work);
+        // the block is dead: drop its lines from L2 without a write-back
+        const char* blk = reinterpret_cast<const char*>(base);
+        for (int64_t b = 0; b < col_block_bytes(spp); b += 128)
+            asm volatile("discard.global.L2 [%0], 128;" ::"l"(blk + b) : "memory");
     }
     const float inv = 1.0f / (float)spp;
     float c[3];

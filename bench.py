@@ -410,7 +410,12 @@ def run_gpu(args):
         "roofline": roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": round(rays_per_step / e2e_s / 1e6, 3), "unit": "Mrays/s",
-                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "frames_in_flight": 2},
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "frames_in_flight": 2,
+                "path": "per frame: the scene table from pinned host memory through rt_batch_update, the batched "
+                        "render (rt_batch_render) and rt_xcorr through the C ABI; the images and C are read back "
+                        "with cudaMemcpyAsync (torch copy_) into pinned host buffers on a second stream, so that "
+                        "one frame's read-back overlaps the next frame's render (rt_render_host renders one scene "
+                        "and waits for its stream, which would serialise the frames)"},
         "xcorr_map": xmap,
         "table1_referenced_fresnel": table1,
         "hd_dp45_1920x1080x16": hd,

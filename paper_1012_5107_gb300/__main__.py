@@ -3,8 +3,8 @@
     python -m paper_1012_5107_gb300 render [--workload small|main|hd|gauss]
         [--kind mirror|bare|cloak] [--precision fp32|fp64]
         [--integrator rk4|dp45|rk4t] [--side N | --width W --height H] [--spp S]
-        [--extent E] [--amplitude A] [--centre-line] [--warmup W] [--repeat K]
-        [--ppm out.ppm]
+        [--extent E] [--amplitude A] [--centre-line] [--variant V] [--min-active M]
+        [--autotune] [--warmup W] [--repeat K] [--ppm out.ppm]
 
 Builds nothing: the CUDA library must have been built (python -c 'import
 __graft_entry__ as g; g.build()').  Each render is one launch through
@@ -76,6 +76,10 @@ def cmd_render(args) -> int:
     sc = rt.Scene(p, tex=tex)
     rgb = torch.zeros(sc.shape, dtype=torch.float32, device="cuda")
     rgb8 = torch.zeros(sc.shape, dtype=torch.uint8, device="cuda")
+    if args.variant is not None or args.min_active:
+        sc.set_launch(-1 if args.variant is None else args.variant, args.min_active or 0)
+    if args.autotune:
+        sc.autotune(rgb, trials=1)
     stream = torch.cuda.Stream()
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
@@ -118,6 +122,9 @@ def main(argv=None) -> int:
     r.add_argument("--extent", type=float)
     r.add_argument("--amplitude", type=float)
     r.add_argument("--centre-line", action="store_true")
+    r.add_argument("--variant", type=int, help="launch variant: 0-2 the per-lane loop, 3 the wavefront loop")
+    r.add_argument("--min-active", type=int, default=0, help="lanes inside the cloak that keep a warp integrating")
+    r.add_argument("--autotune", action="store_true", help="time the launch configurations first and keep the fastest")
     r.add_argument("--warmup", type=int, default=1)
     r.add_argument("--repeat", type=int, default=3)
     r.add_argument("--ppm")

@@ -201,6 +201,15 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
     s->cf.fk = (float)s->cd.fk;
     s->cd.is2 = 1.0 / (s->idx_scale * s->idx_scale);
     s->cf.is2 = (float)s->cd.is2;
+    // RK4 moves a ray by |h p + h^2/6 (F1 + F2 + F3)| <= h |p|max + h^2 |F|max / 2 a step,
+    // with |p| = n <= s / (1 - kA) (|1 + W0| >= 1 - |W0| > 1 - kA) and
+    // |F| = k s^2 |W0| n^4 <= k s^2 kA / (1 - kA)^4; a thousandth of slack on |p|
+    {
+        const double sc2 = s->idx_scale, q = 1.0 - s->kA;
+        const double pmax = 1.001 * sc2 / q, fmax = kTwoPi * sc2 * sc2 * s->kA / (q * q * q * q);
+        s->cd.isafe = 1.0 / (s->h * pmax + 0.5 * s->h * s->h * fmax);
+        s->cf.isafe = (float)(s->cd.isafe * (1.0 - 1e-6));
+    }
     s->cd.ybot = ((d->flags & RT_FLAG_PLATE) || d->mirror == RT_MIRROR_GAUSS) ? 0.0 : -s->A;
     s->cf.ybot = (float)s->cd.ybot;
     // Gaussian bump: width, 1/width, k h, h/width, the Newton stop on W and
@@ -298,7 +307,7 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     build_dev(desc, &s->dev);
     int bps = 0;
     s->variant = kDefaultVariant;
-    s->min_active = kMinActive;
+    s->min_active = default_min_active(desc->integrator);
     s->wait = WaitLimit{kDefaultWaitSpin, 0};
     cudaError_t e = desc->mirror == RT_MIRROR_GAUSS ? gauss_upload() : cudaSuccess;
     if (e == cudaSuccess) e = render_occupancy(desc->precision, render_mode(*desc), s->variant, desc->flags != 0, &bps);
@@ -457,7 +466,7 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
     char key[160];
     snprintf(key, sizeof key, "scene/p%d/i%d/c%d/m%d/f%d/log2n%d", d.precision, d.integrator, d.cloak, d.mirror, d.flags,
              (int)floor(log2(samples > 1.0 ? samples : 1.0)));
-    int v = kDefaultVariant, m = kMinActive;
+    int v = kDefaultVariant, m = default_min_active(d.integrator);
     if (!tune_lookup(key, &v, &m)) {
         const int cand[] = {12, 16, 20, 24, 28};
         cudaStream_t st = (cudaStream_t)stream;

@@ -35,6 +35,7 @@ struct StepConst {
     // stop |dW|^2 <= gtol, and the largest Newton step |dW|^2 <= gcap2
     R gw, igw, gkh, gq, gtol, gcap2;
     R gpred;     // Gaussian bump: a step continues the medium when |dz|^2 / w_b^2 <= gpred
+    R isafe;     // RK4 in the grating cloak: 1 / (the largest move of one step), see box_step_into
 };
 
 // Hot counters of a lane, kept in registers.

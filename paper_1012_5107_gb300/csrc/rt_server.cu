@@ -222,7 +222,7 @@ static cudaError_t ring_launch_t(int grid, RingSlot* slots, RingCtl* ctl, RingDo
         set.fetch_or(bit);
     }
     wave_ring_kernel<R, INTEG><<<grid, kWaveBlock, wave_smem_bytes<R>(), st>>>(slots, ctl, done, counters,
-                                                                               kMinActive);
+                                                                               default_min_active(INTEG));
     return cudaGetLastError();
 }
 

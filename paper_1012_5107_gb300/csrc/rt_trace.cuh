@@ -1496,7 +1496,7 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
                     nx = (double)k.kA * (double)sn;
                     ny = 1.0 - (double)k.kA * (double)cs;
                 }
-                const double il = 1.0 / sqrt(nx * nx + ny * ny);
+                const double il = rsqrt_nr(nx * nx + ny * ny);
                 double d[3];
                 air_dir(C, d);
                 const double pn = (d[0] * nx + d[1] * ny) * il;
@@ -1641,7 +1641,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     }
     double d[3], l2 = 0.0;
     for (int a = 0; a < 3; ++a) { d[a] = pt[a] + pout * N[a]; l2 += d[a] * d[a]; }
-    const double il = 1.0 / sqrt(l2);
+    const double il = rsqrt_nr(l2);
     C.cx = b.cx;
     C.X = b.X;
     if constexpr (gauss_of(INTEG)) {          // back to cell + fraction in air
@@ -1665,9 +1665,24 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
 // non-finite (PH_EVENT) or hits the step cap (PH_GUARD) leaves the state in s
 // and o undefined.  Writing into a second state lets the caller alternate
 // between two states instead of copying the new one back every step.
+// RK4 in the grating cloak skips the box faces' tests while the ray is
+// farther from every face than `safe` steps can move it (isafe: one over the
+// largest move of a step); the grating's test runs every step.
+template <int INTEG>
+__host__ __device__ constexpr bool face_skip() { return integ_of(INTEG) == RT_RK4 && !gauss_of(INTEG); }
+
+template <class R>
+__device__ __forceinline__ int safe_steps(const StepConst<R>& k, const Box<R>& o)
+{
+    const R dx = k.E2 - fabs(o.cx + o.X), dz = k.E2 - fabs(o.z), dy = k.ytop - o.y;
+    const R d = fmin(dy, fmin(dx, dz));
+    return (int)(d * k.isafe) - 1;
+}
+
 template <class R, int INTEG>
 __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& s,
-                                              Box<R>& o, int& phase, int& surf, int& steps, LaneStats& st)
+                                              Box<R>& o, int& phase, int& surf, int& steps, LaneStats& st,
+                                              int& safe)
 {
     if (steps >= max_steps) {
         phase = PH_GUARD;
@@ -1723,11 +1738,19 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
         st.steps++;
     }
     const R gG = o.y + o.wr * R(kInvTwoPi);
+    if constexpr (face_skip<INTEG>()) {
+        if (safe > 0 && gG >= R(0)) {
+            --safe;
+            surf = EV_NONE;
+            return;
+        }
+    }
     const R gT = k.ytop - o.y;
     const R gXp = (k.E2 - o.cx) - o.X, gXm = (k.E2 + o.cx) + o.X;
     const R gZp = k.E2 - o.z, gZm = k.E2 + o.z;
     if (gG >= R(0) && gT >= R(0) && gXp >= R(0) && gXm >= R(0) && gZp >= R(0) && gZm >= R(0)) {
         surf = EV_NONE;
+        if constexpr (face_skip<INTEG>()) safe = safe_steps(k, o);
         return;
     }
     // crossed a surface (or went non-finite): the service pass locates it from s
@@ -1742,13 +1765,13 @@ __device__ __forceinline__ void box_step_into(const StepConst<R>& k, int64_t max
     phase = PH_EVENT;
 }
 
-// One step of b in place (the per-lane loop).
+// One step of b in place.
 template <class R, int INTEG>
 __device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& b, int& phase,
-                                         int& surf, int& steps, LaneStats& st)
+                                         int& surf, int& steps, LaneStats& st, int& safe)
 {
     Box<R> o;
-    box_step_into<R, INTEG>(k, max_steps, C, b, o, phase, surf, steps, st);
+    box_step_into<R, INTEG>(k, max_steps, C, b, o, phase, surf, steps, st, safe);
     if (phase == PH_BOX) b = o;
 }
 
@@ -2024,6 +2047,7 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
 #endif
         // once the work is exhausted, refills are pointless: step while any lane is inside
         const int need = __any_sync(0xffffffffu, phase == PH_EXIT) ? 1 : min_active;
+        int safe = 0;                              // steps without the faces' tests (box_step_into)
         for (;;) {
 #if RT_PROFILE
             prof_iters += 1;
@@ -2031,7 +2055,7 @@ __device__ __forceinline__ void render_loop(const Src& src, unsigned long long* 
 #endif
             if (phase == PH_BOX) {
                 const DevScene& sc = src.scene(C.scene);
-                box_step<R, INTEG>(step_const<R>(sc), sc.max_steps, C, b, phase, surf, steps, st);
+                box_step<R, INTEG>(step_const<R>(sc), sc.max_steps, C, b, phase, surf, steps, st, safe);
             }
             if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
         }

@@ -304,11 +304,12 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
                 kp = &kc;
             }
             const int64_t max_steps = sc.max_steps;
+            int safe = 0;                          // steps without the faces' tests (box_step_into)
             for (int it = 0; it < kWaveTaskSteps; ++it) {
 #if RT_PROFILE
                 prof[2] += 1;
 #endif
-                if (phase == PH_BOX) box_step<R, INTEG>(*kp, max_steps, C, b, phase, surf, steps, st);
+                if (phase == PH_BOX) box_step<R, INTEG>(*kp, max_steps, C, b, phase, surf, steps, st, safe);
                 if (__popc(__ballot_sync(0xffffffffu, phase == PH_BOX)) < need) break;
             }
             if (p >= 0) {

@@ -209,6 +209,16 @@ static void build_dev(const rt_scene_desc* d, DevScene* s)
         const double pmax = 1.001 * sc2 / q, fmax = kTwoPi * sc2 * sc2 * s->kA / (q * q * q * q);
         s->cd.isafe = 1.0 / (s->h * pmax + 0.5 * s->h * s->h * fmax);
         s->cf.isafe = (float)(s->cd.isafe * (1.0 - 1e-6));
+        // a full RK4 step's second stage lies h/2 |p| from its start and its
+        // fourth at least h/2 |p| - 3/4 h^2 |F| from its third, with
+        // |p| >= s / (1 + kA) and |1/(1 + W0)|^2 >= 1 / (1 + kA)^2: if even
+        // the shortest of those distances is beyond the continuation's reach
+        // (kPredTol, with a factor 4 of margin), those stages always solve
+        const double nmin = 1.0 / (1.0 + s->kA), pmin = sc2 * nmin;
+        const double d = std::min(0.5 * s->h * pmin, 0.5 * s->h * pmin - 0.75 * s->h * s->h * fmax);
+        const double reach = d > 0.0 ? d * d * nmin * nmin : 0.0;
+        s->cf.far24 = reach > 4.0 * (double)Mth<float>::kPredTol ? 1.0f : 0.0f;
+        s->cd.far24 = reach > 4.0 * Mth<double>::kPredTol ? 1.0 : 0.0;
     }
     s->cd.ybot = ((d->flags & RT_FLAG_PLATE) || d->mirror == RT_MIRROR_GAUSS) ? 0.0 : -s->A;
     s->cf.ybot = (float)s->cd.ybot;

@@ -36,6 +36,8 @@ struct StepConst {
     R gw, igw, gkh, gq, gtol, gcap2;
     R gpred;     // Gaussian bump: a step continues the medium when |dz|^2 / w_b^2 <= gpred
     R isafe;     // RK4 in the grating cloak: 1 / (the largest move of one step), see box_step_into
+    R far24;     // RK4 in the grating cloak: 1 if a full step's second and fourth stage points always lie too
+                 // far from the previous point for W0 to be continued without a solve (see med_stage)
 };
 
 // Hot counters of a lane, kept in registers.

@@ -333,16 +333,29 @@ __device__ __forceinline__ void med_force(const StepConst<R>& k, Box<R>& b)
 // force at the new point goes to (Fx, Fy).
 // (gpr, gpi): the Gaussian medium's second derivative of dw/dz at the
 // previous point in, at the new one out (zero when unknown).
+// `far`: the point is known to lie beyond the continuation's reach (the
+// second and fourth stages of a full RK4 step, StepConst::far24), so W0 is
+// predicted and solved without testing the distance: the same arithmetic as
+// w0_continue's solving branch.
 template <class R, int INTEG>
 __device__ __forceinline__ bool med_stage(const StepConst<R>& k, R X, R y, R dx, R dy, R& wr, R& wi, R& rr, R& ri,
-                                          R Fpx, R Fpy, R& Fx, R& Fy, R& gpr, R& gpi, LaneStats& st)
+                                          R Fpx, R Fpy, R& Fx, R& Fy, R& gpr, R& gpi, LaneStats& st,
+                                          bool far = false)
 {
     if constexpr (gauss_of(INTEG)) {
         Fx = Fpx;
         Fy = Fpy;
         return gauss_continue(k, X, y, dx, dy, wr, wi, rr, ri, Fx, Fy, gpr, gpi, st);
     } else {
-        const bool solved = w0_continue(k, X, y, dx, dy, wr, wi, rr, ri, st);
+        bool solved;
+        if (far) {
+            if constexpr (sizeof(R) == 4) w0_predict(wr, wi, rr, ri, dx, dy);
+            else w0_predict3(wr, wi, rr, ri, dx, dy);
+            w0_eval(k, X, y, wr, wi, rr, ri, st);
+            solved = true;
+        } else {
+            solved = w0_continue(k, X, y, dx, dy, wr, wi, rr, ri, st);
+        }
         ray_force(wr, wi, rr, ri, k.fk, Fx, Fy);
         return solved;
     }
@@ -411,6 +424,8 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     if constexpr (sizeof(R) == 4) {
         // the same step with the (x, y) arithmetic in packed pairs
         const float h2 = 0.5f * h;
+        // a full step's second and fourth stages always solve (StepConst::far24)
+        const bool far = (k.far24 != 0.0f) & (h == k.h);
         float wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
         const float2 P = p2(s.X, s.y), M = p2(s.px, s.py), F1 = p2(s.Fx, s.Fy);
         const float2 H2 = p2s(h2), H = p2s(h);
@@ -419,7 +434,7 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
         const float2 P2 = fma2(H2, M, P);
         float F2x, F2y, gpr = 0.0f, gpi = 0.0f;
         bool solved = med_stage<R, INTEG>(k, P2.x, P2.y, D2.x, D2.y, wr, wi, rr, ri, s.Fx, s.Fy, F2x, F2y, gpr,
-                                          gpi, st);
+                                          gpi, st, far);
         // stage 3 at r + h/2 (p + h/2 F1)
         const float2 P3 = fma2(H2, fma2(H2, F1, M), P);
         const float2 D3 = sub2(P3, P2);
@@ -430,7 +445,8 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
         const float2 P4 = fma2(H, fma2(H2, Fs2, M), P);
         const float2 D4 = sub2(P4, P3);
         float F4x, F4y;
-        solved |= med_stage<R, INTEG>(k, P4.x, P4.y, D4.x, D4.y, wr, wi, rr, ri, F3x, F3y, F4x, F4y, gpr, gpi, st);
+        solved |= med_stage<R, INTEG>(k, P4.x, P4.y, D4.x, D4.y, wr, wi, rr, ri, F3x, F3y, F4x, F4y, gpr, gpi, st,
+                                      far);
         // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
         const float h6 = h * (1.0f / 6.0f), hh6 = h * h6;
         const float2 Fs3 = p2(F3x, F3y), Fs4 = p2(F4x, F4y);
@@ -453,12 +469,13 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
         return;
     }
     const R h2 = R(0.5) * h;
+    const bool far = (k.far24 != R(0)) & (h == k.h);
     R wr = s.wr, wi = s.wi, rr = s.rr, ri = s.ri;
     // stage 2 at r + h/2 p
     const R X2 = s.X + h2 * s.px, y2 = s.y + h2 * s.py;
     R F2x, F2y, gpr = R(0), gpi = R(0);
     bool solved = med_stage<R, INTEG>(k, X2, y2, h2 * s.px, h2 * s.py, wr, wi, rr, ri, s.Fx, s.Fy, F2x, F2y, gpr, gpi,
-                                      st);
+                                      st, far);
     // stage 3 at r + h/2 (p + h/2 F1), (h/2)^2 F1 away from stage 2
     const R X3 = s.X + h2 * (s.px + h2 * s.Fx), y3 = s.y + h2 * (s.py + h2 * s.Fy);
     R F3x, F3y;
@@ -466,7 +483,7 @@ __device__ __forceinline__ void rk4_step(const StepConst<R>& k, const Box<R>& s,
     // stage 4 at r + h (p + h/2 F2)
     const R X4 = s.X + h * (s.px + h2 * F2x), y4 = s.y + h * (s.py + h2 * F2y);
     R F4x, F4y;
-    solved |= med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, F3x, F3y, F4x, F4y, gpr, gpi, st);
+    solved |= med_stage<R, INTEG>(k, X4, y4, X4 - X3, y4 - y3, wr, wi, rr, ri, F3x, F3y, F4x, F4y, gpr, gpi, st, far);
     // position increment h p + h^2/6 (F1 + F2 + F3), momentum h/6 (F1 + 2F2 + 2F3 + F4)
     const R h6 = h * R(1.0 / 6.0), hh6 = h * h6;
     const R dX = h * s.px + hh6 * (s.Fx + F2x + F3x);

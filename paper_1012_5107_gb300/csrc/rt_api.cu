@@ -376,7 +376,7 @@ static int render_common(rt_scene* s, const int64_t* d_pix, int64_t nwork, float
            "scene options (RT_FLAG_*) are rendered by the wavefront loop (variant %d) only", kVariantWave);
     SampleScratch ss = {nullptr, nullptr, nullptr};
     if (nwork > 0 && (s->desc.flags & RT_FLAG_FRESNEL)) {
-        const size_t bytes = branch_queue_bytes(s->desc.precision, s->grid);
+        const size_t bytes = branch_queue_bytes(s->desc.precision, s->desc.integrator, s->grid);
         if (bytes > s->branch_cap) {
             RT_CK(cudaStreamWaitEvent(st, s->done, 0));
             if (s->d_branch) RT_CK(cudaFreeAsync(s->d_branch, st));

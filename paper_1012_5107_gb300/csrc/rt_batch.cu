@@ -28,7 +28,7 @@ static cudaError_t batch_prepare()
     const unsigned long long bit = 1ull << (dev & 63);
     if (done.load() & bit) return cudaSuccess;
     e = cudaFuncSetAttribute(wave_batch_kernel<R, INTEG, OPT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)wave_smem_bytes<R>());
+                             (int)wave_smem_bytes<R, INTEG>());
     if (e == cudaSuccess) done.fetch_or(bit);
     return e;
 }
@@ -38,8 +38,8 @@ static cudaError_t batch_occupancy_t(int* bps)
 {
     const cudaError_t e = batch_prepare<R, INTEG, OPT>();
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_batch_kernel<R, INTEG, OPT>, kWaveBlock,
-                                                         wave_smem_bytes<R>());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_batch_kernel<R, INTEG, OPT>,
+                                                         WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>());
 }
 
 template <bool OPT>
@@ -66,7 +66,7 @@ static cudaError_t launch_batch_t(const BatchLaunch& L, cudaStream_t stream)
 {
     const cudaError_t e = batch_prepare<R, INTEG, OPT>();
     if (e != cudaSuccess) return e;
-    wave_batch_kernel<R, INTEG, OPT><<<L.grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+    wave_batch_kernel<R, INTEG, OPT><<<L.grid, WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>(), stream>>>(
         L.scenes, L.offsets, L.soffsets, L.rgbs, L.n, L.total, L.total_samples, L.scratch.col, L.scratch.cnt,
         L.scratch.br, L.counters, L.min_active);
     return cudaGetLastError();
@@ -273,7 +273,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     }
     b->grid = (bps > 0 ? bps : 1) * b->nsm;
     if (fresnel) {
-        e = cudaMalloc(&b->d_br, branch_queue_bytes(precision, b->grid));
+        e = cudaMalloc(&b->d_br, branch_queue_bytes(precision, integrator, b->grid));
         if (e != cudaSuccess) {
             set_error("rt_batch_create: %s", cudaGetErrorString(e));
             rt_batch_destroy(b);

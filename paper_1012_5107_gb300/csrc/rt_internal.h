@@ -56,8 +56,9 @@ struct SampleScratch {
     int* cnt;
     void* br;        // Fresnel branch queues (RT_FLAG_FRESNEL), see wave_branch_bytes
 };
-// Bytes of the Fresnel branch queues a wavefront launch of `grid` blocks needs.
-size_t branch_queue_bytes(int precision, int grid);
+// Bytes of the Fresnel branch queues a wavefront launch of `grid` blocks of
+// this precision and integrator needs.
+size_t branch_queue_bytes(int precision, int integrator, int grid);
 constexpr size_t kScratchBytesPerSample = 3 * sizeof(float);
 constexpr size_t kScratchBytesPerPixel = sizeof(int);
 // The colours of a pixel's samples sit in one block of whole 128-byte L2

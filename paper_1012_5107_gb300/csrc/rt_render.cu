@@ -27,7 +27,7 @@ template <class R, int INTEG, bool OPT>
 static cudaError_t wave_prepare()
 {
     static std::atomic<unsigned long long> done{0};
-    return allow_smem(wave_kernel<R, INTEG, OPT>, wave_smem_bytes<R>(), done);
+    return allow_smem(wave_kernel<R, INTEG, OPT>, wave_smem_bytes<R, INTEG>(), done);
 }
 
 // Register-budget variants of the per-lane loop are compiled for the FP32 RK4
@@ -43,14 +43,15 @@ static cudaError_t occupancy_t(int variant, bool opt, int* bps)
             if (opt) {
                 const cudaError_t e = wave_prepare<R, INTEG, true>();
                 if (e != cudaSuccess) return e;
-                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, true>, kWaveBlock,
-                                                                     wave_smem_bytes<R>());
+                return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, true>,
+                                                                     WaveShape<R, INTEG>::kBlock,
+                                                                     wave_smem_bytes<R, INTEG>());
             }
         }
         const cudaError_t e = wave_prepare<R, INTEG, false>();
         if (e != cudaSuccess) return e;
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, false>, kWaveBlock,
-                                                             wave_smem_bytes<R>());
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_kernel<R, INTEG, false>,
+                                                             WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>());
     }
     if constexpr (integ_of(INTEG) == RT_RK4T || gauss_of(INTEG)) {
         return cudaErrorInvalidValue;                // the wavefront loop only
@@ -77,14 +78,14 @@ static cudaError_t launch_t(const DevScene& sc, int variant, int min_active, flo
             if (sc.flags) {
                 const cudaError_t e = wave_prepare<R, INTEG, true>();
                 if (e != cudaSuccess) return e;
-                wave_kernel<R, INTEG, true><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+                wave_kernel<R, INTEG, true><<<grid, WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>(), stream>>>(
                     sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br, WaveWait{wl.spin, wl.hold});
                 return cudaGetLastError();
             }
         }
         const cudaError_t e = wave_prepare<R, INTEG, false>();
         if (e != cudaSuccess) return e;
-        wave_kernel<R, INTEG, false><<<grid, kWaveBlock, wave_smem_bytes<R>(), stream>>>(
+        wave_kernel<R, INTEG, false><<<grid, WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>(), stream>>>(
             sc, rgb, rgb8, rec, counters, min_active, ss.col, ss.cnt, ss.br, WaveWait{wl.spin, wl.hold});
         return cudaGetLastError();
     }
@@ -152,9 +153,11 @@ cudaError_t gauss_upload()
     return e;
 }
 
-size_t branch_queue_bytes(int precision, int grid)
+size_t branch_queue_bytes(int precision, int integrator, int grid)
 {
-    return precision == RT_FP64 ? wave_branch_bytes<double>(grid) : wave_branch_bytes<float>(grid);
+    if (precision == RT_FP64) return wave_branch_bytes<double, RT_RK4>(grid);
+    return integ_of(integrator) == RT_DP45 ? wave_branch_bytes<float, RT_DP45>(grid)
+                                           : wave_branch_bytes<float, RT_RK4>(grid);
 }
 
 bool variant_compiled(int precision, int integrator, int variant)

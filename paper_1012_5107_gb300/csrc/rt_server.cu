@@ -199,7 +199,7 @@ struct RingScenes {
 };
 
 template <class R, int INTEG>
-__global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_ring_kernel(
+__global__ void __launch_bounds__(WaveShape<R, INTEG>::kBlock, WaveShape<R, INTEG>::kMinBlocks) wave_ring_kernel(
     RingSlot* slots, RingCtl* ctl, RingDone* done, unsigned long long* counters, int min_active)
 {
     const RingScenes src{slots, ctl, done, nullptr};
@@ -217,11 +217,11 @@ static cudaError_t ring_launch_t(int grid, RingSlot* slots, RingCtl* ctl, RingDo
     const unsigned long long bit = 1ull << (dev & 63);
     if (!(set.load() & bit)) {
         e = cudaFuncSetAttribute(wave_ring_kernel<R, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)wave_smem_bytes<R>());
+                                 (int)wave_smem_bytes<R, INTEG>());
         if (e != cudaSuccess) return e;
         set.fetch_or(bit);
     }
-    wave_ring_kernel<R, INTEG><<<grid, kWaveBlock, wave_smem_bytes<R>(), st>>>(slots, ctl, done, counters,
+    wave_ring_kernel<R, INTEG><<<grid, WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>(), st>>>(slots, ctl, done, counters,
                                                                                default_min_active(INTEG));
     return cudaGetLastError();
 }
@@ -230,10 +230,10 @@ template <class R, int INTEG>
 static cudaError_t ring_occupancy_t(int* bps)
 {
     cudaError_t e = cudaFuncSetAttribute(wave_ring_kernel<R, INTEG>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)wave_smem_bytes<R>());
+                                         (int)wave_smem_bytes<R, INTEG>());
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_ring_kernel<R, INTEG>, kWaveBlock,
-                                                         wave_smem_bytes<R>());
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(bps, wave_ring_kernel<R, INTEG>,
+                                                         WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>());
 }
 
 static int kind_of(int precision, int integrator) { return precision * 3 + integrator; }

@@ -33,27 +33,37 @@
 
 namespace grt {
 
-constexpr int kWaveBlock = 256;
 constexpr int kWaveTaskSteps = 256;          // step cap of one integration task
 constexpr int kWaveSpin = kDefaultWaitSpin;  // attempts (with a short sleep) before a wait gives up
 
-// Pixels in flight per block: more than the block's lanes, so that a warp
-// always finds work while the other warps hold theirs.
-template <class R> struct WavePool {
-    static constexpr int P = sizeof(R) == 4 ? 384 : 320;
+// The block shape of the loop for a precision and integrator: threads per
+// block, blocks per SM (which sets the registers a thread may use: 65536 /
+// (threads x blocks)) and P, the samples in flight per block -- more than the
+// block's lanes, so that a warp always finds work while the other warps hold
+// theirs.  FP32 RK4: two blocks of 256 threads, 128 registers.  FP32
+// Dormand-Prince keeps the running sums of its stages and two states live
+// through a step, which spills at 128 registers: one block of 384 threads
+// (12 warps, up to 168 registers).  FP64: one block of 256 threads.
+template <class R, int INTEG>
+struct WaveShape {
+    static constexpr bool kWide = sizeof(R) == 4 && integ_of(INTEG) == RT_DP45;
+    static constexpr int kBlock = kWide ? 384 : 256;
+    static constexpr int kMinBlocks = (sizeof(R) == 4 && !kWide) ? 2 : 1;
+    static constexpr int P = kWide ? 576 : (sizeof(R) == 4 ? 384 : 320);
 };
 
-template <class R>
+template <class R, int INTEG>
 constexpr size_t wave_smem_bytes()
 {
-    return (sizeof(Cold<R>) + sizeof(Box<R>)) * WavePool<R>::P + 3 * sizeof(short) * WavePool<R>::P;
+    constexpr int P = WaveShape<R, INTEG>::P;
+    return (sizeof(Cold<R>) + sizeof(Box<R>)) * P + 3 * sizeof(short) * P;
 }
 
 // Bytes of the Fresnel branch queues of a launch of `grid` blocks.
-template <class R>
+template <class R, int INTEG>
 constexpr size_t wave_branch_bytes(int grid)
 {
-    return (size_t)grid * WavePool<R>::P * kMaxBranches * sizeof(Branch<R>);
+    return (size_t)grid * WaveShape<R, INTEG>::P * kMaxBranches * sizeof(Branch<R>);
 }
 
 struct WaveCtl {
@@ -179,7 +189,7 @@ __device__ __forceinline__ void wave_finish_sample(const Src& src, const DevScen
 template <class R, int INTEG, bool OPT, class Src>
 __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* counters, int min_active, WaveWait ww)
 {
-    constexpr int P = WavePool<R>::P;
+    constexpr int P = WaveShape<R, INTEG>::P;
     extern __shared__ __align__(16) unsigned char wave_smem[];
     Cold<R>* cold = reinterpret_cast<Cold<R>*>(wave_smem);
     Box<R>* boxes = reinterpret_cast<Box<R>*>(wave_smem + sizeof(Cold<R>) * P);
@@ -410,13 +420,8 @@ __device__ __forceinline__ void wave_loop(const Src& src, unsigned long long* co
 #endif
 }
 
-// Two blocks of 256 threads per SM in FP32 (at most 128 registers a thread),
-// one in FP64 (whose pool does not fit twice).
-template <class R>
-constexpr int wave_min_blocks() { return sizeof(R) == 4 ? 2 : 1; }
-
 template <class R, int INTEG, bool OPT>
-__global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_kernel(const __grid_constant__ DevScene sc,
+__global__ void __launch_bounds__(WaveShape<R, INTEG>::kBlock, WaveShape<R, INTEG>::kMinBlocks) wave_kernel(const __grid_constant__ DevScene sc,
                                                             float* __restrict__ rgb, uint8_t* __restrict__ rgb8,
                                                             rt_ray_record* rec, unsigned long long* counters,
                                                             int min_active, float* samp_col, int* pix_cnt,
@@ -427,7 +432,7 @@ __global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_kernel(
 }
 
 template <class R, int INTEG, bool OPT>
-__global__ void __launch_bounds__(kWaveBlock, wave_min_blocks<R>()) wave_batch_kernel(
+__global__ void __launch_bounds__(WaveShape<R, INTEG>::kBlock, WaveShape<R, INTEG>::kMinBlocks) wave_batch_kernel(
     const DevScene* __restrict__ scenes, const int64_t* __restrict__ offsets, const int64_t* __restrict__ soffsets,
     float* const* __restrict__ rgbs, int n, int64_t total, int64_t total_samples, float* samp_col, int* pix_cnt,
     void* branches, unsigned long long* counters, int min_active)

@@ -19,8 +19,9 @@ constexpr int kVariantWave = 3;
 constexpr int kDefaultVariant = kVariantWave;
 constexpr int kMinActive = 28;   // an integration task continues while at least this many of its 32 rays are inside the cloak
 // Dormand-Prince steps are longer: a task holding fewer rays is still worth
-// running (1920 x 1080 x 16, E = 8: 163 ms at 28, 144 ms at 12, 146 ms at 20)
-constexpr int kMinActiveDP45 = 16;
+// running (1920 x 1080 x 16 with one block of 384 threads per SM, E = 8 / 32:
+// 133.0 / 214.8 ms at 8, 135.1 / 221.5 ms at 16; 2 to 10 within 1 %)
+constexpr int kMinActiveDP45 = 8;
 inline int default_min_active(int integrator) { return integrator == RT_DP45 ? kMinActiveDP45 : kMinActive; }
 constexpr int kMaxWindows = 16;
 // Render mode: the integrator (RT_RK4, RT_DP45, RT_RK4T), with kModeGauss set

@@ -877,6 +877,16 @@ __device__ __forceinline__ void face_normal(int ev, R N[3])
     else N[1] = R(-1);
 }
 
+// Whether a trial step's end point needs a W0 solve: RK4 only continues W0
+// to its end point; the FP32 Dormand-Prince step has already solved it there
+// (or continued it exactly to FP32), as its last stage.  The FP64 path solves
+// again, as it always did, to keep its rays on the oracle's to 1e-12.
+template <class R, int INTEG>
+__host__ __device__ constexpr bool resolve_end()
+{
+    return !(sizeof(R) == 4 && integ_of(INTEG) == RT_DP45);
+}
+
 // Root theta in (0, 1] of g_ev(Phi_{theta h}(b)) given its value g1 < 0 at
 // theta = 1 (the zero at theta = 0 divided out when the step starts on that
 // surface).  First guess from the quadratic through g(0), g'(0) and g(1);
@@ -917,7 +927,8 @@ __device__ R locate_event(const StepConst<R>& k, const Box<R>& b, R h, int ev, b
     int side = 0;
     for (int it = 0; it < Mth<R>::kEventIt; ++it) {
         integ_step<R, INTEG>(k, b, th * h, t, st);
-        med_solve<R, INTEG>(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, t.Fx, t.Fy, st);
+        if constexpr (resolve_end<R, INTEG>())
+            med_solve<R, INTEG>(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, t.Fx, t.Fy, st);
         const R g = event_g(k, ev, t);
         if (fabs(g) <= Mth<R>::kEventTol) return th;
         const R gd = on_surface ? g / th : g;
@@ -1567,7 +1578,8 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
     }
     if (last != ev_best) {
         integ_step<R, INTEG>(k, b, th_best * C.hs, t, st);
-        med_solve<R, INTEG>(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, t.Fx, t.Fy, st);
+        if constexpr (resolve_end<R, INTEG>())
+            med_solve<R, INTEG>(k, t.X, t.y, t.wr, t.wi, t.rr, t.ri, t.Fx, t.Fy, st);
     }
     const R hc = b.hc;
     b = t;

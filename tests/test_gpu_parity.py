@@ -205,10 +205,13 @@ def test_render_small_config(rt, torch, orc, precision, kind):
 def test_render_main_config_sampled(rt, torch, orc, precision):
     """512 x 512, 4 stratified samples per pixel: the full render in the
     launch configuration the benchmark times, checked on a seeded subset of
-    pixels that the oracle traces one by one."""
+    pixels that the oracle traces one by one.  6000 pixels (24000 rays): at
+    the FP32 path's measured rate of rays outside the tolerance (0.063 % of
+    the render's 1,048,576), 6000 rays would hold the 0.1 % bar only within
+    their sampling noise (3.8 expected against 6 allowed)."""
     p = inputs.three_renders(inputs.config_main(precision=precision))["cloak"]
     g = gpu_render(rt, torch, p)
-    pix = inputs.pixel_subset(512, 512, 1500, seed=21)
+    pix = inputs.pixel_subset(512, 512, 6000, seed=21)
     o_rgb, o_rec = orc.render_pixels(orc.Scene(p), pix, records=True)
     grec = g["rec"].reshape(512 * 512, 4)[pix]
     if precision == 1:

@@ -699,11 +699,14 @@ def bench_batch(rt, torch, stream) -> dict:
             "Gsteps_per_s": round(st["steps"] / ms / 1e6, 3), "min_active": m, "autotune_s": round(tune_s, 2)}
 
 
-def serve_leg(rt, torch, rate: float, count: int, seed: int = 5) -> dict:
+def serve_leg(rt, torch, rate: float, count: int, seed: int = 5, rays_per_s: float | None = None) -> dict:
     """Serve `count` requests arriving as a Poisson process of mean rate `rate`
     (seed `seed`; side log-uniform in [256, 2048], spp log-uniform in [1, 64],
     scenes as in the batch workload) under a 40 GB ray-state budget; latency is
-    submission to completion."""
+    submission to completion.  Requests span 65 thousand to 268 million rays,
+    so latency percentiles mostly sort requests by size: with `rays_per_s`
+    (the server's capacity) each request's slowdown is its latency over its
+    rays at that rate, and the leg reports the slowdown's percentiles too."""
     reqs = inputs.serving_requests(count, seed=seed, rate=rate, precision=inputs.FP32)
     imgs = [torch.zeros((p["height"], p["width"], 3), dtype=torch.float32, device="cuda") for _, p in reqs]
     server = rt.Server(budget_bytes=40 * 10**9, max_inflight=2)
@@ -730,12 +733,20 @@ def serve_leg(rt, torch, rate: float, count: int, seed: int = 5) -> dict:
     server.close()
     lat = np.array([r["latency_ms"] for r in res.values()])
     rays = sum(r["rays"] for r in res.values())
+    slow = None
+    if rays_per_s:
+        alone = np.array([r["rays"] / rays_per_s * 1e3 for r in res.values()])
+        sd = lat / np.maximum(alone, 1e-6)
+        slow = {"p50": round(float(np.percentile(sd, 50)), 2), "p99": round(float(np.percentile(sd, 99)), 2),
+                "of_largest_1pc": round(float(np.median(sd[alone >= np.percentile(alone, 99)])), 2)}
     p50, p99 = float(np.percentile(lat, 50)), float(np.percentile(lat, 99))
     out = {"requests": len(reqs), "completed": len(res), "failed": sum(r["status"] != 0 for r in res.values()),
            "arrival_rate_per_s": round(rate, 3), "p50_ms": round(p50, 2), "p99_ms": round(p99, 2),
            "p99_over_p50": round(p99 / p50, 2), "mean_ms": round(float(lat.mean()), 2),
            "Mrays_per_s": round(rays / wall / 1e6, 3), "wall_s": round(wall, 2), "max_queued": max_queued,
            "mean_rays_per_request": round(rays / max(len(res), 1))}
+    if slow is not None:
+        out["slowdown"] = slow
     del imgs
     torch.cuda.empty_cache()
     return out
@@ -754,7 +765,8 @@ def bench_serving(rt, torch) -> dict:
     out["offered_200_per_s"] = sat
     capacity = sat["Mrays_per_s"] * 1e6 / sat["mean_rays_per_request"]
     out["max_sustainable_req_per_s"] = round(capacity, 2)
-    out["load_80_percent"] = serve_leg(rt, torch, rate=0.8 * capacity, count=200)
+    out["load_80_percent"] = serve_leg(rt, torch, rate=0.8 * capacity, count=200,
+                                       rays_per_s=sat["Mrays_per_s"] * 1e6)
     return out
 
 

@@ -330,7 +330,10 @@ int rt_validate_desc(const rt_scene_desc* desc);
  * requests in arrival order while the sum of their ray-state footprints
  * (76 bytes per sample: 64 of ray state and a 12-byte colour slot; 16 bytes
  * per pixel: the float output image and a sample counter; see
- * rt_request_bytes) stays within the budget, and publishes each admitted
+ * rt_request_bytes) stays within the budget.  A request that fits may pass
+ * queued requests that do not fit yet (so that a small request does not wait
+ * behind a large one for the budget), but no request is passed more than 32
+ * times; the worker looks 64 requests deep.  It publishes each admitted
  * request into a ring of request slots in device memory (one ring per
  * precision and integrator, 1024 requests in flight each).  A persistent
  * launch of the wavefront loop takes samples from the ring up to the

@@ -50,7 +50,7 @@ namespace grt {
 
 constexpr int kRingSlots = 1024;          // requests a ring holds in flight
 constexpr int kRingGrabTries = 4096;      // scans of one grab before it gives up
-constexpr int kRingWindow = 16;           // oldest requests with samples left that a grab chooses from
+constexpr int kRingWindow = 64;           // oldest requests with samples left that a grab chooses from
 constexpr int kRingLocalBits = 40;        // a grabbed sample: slot << 40 | its index in the request
 constexpr int kRingKinds = 6;             // precision x integrator (RK4, DP45, RK4T)
 
@@ -101,66 +101,76 @@ struct RingScenes {
     void* branches;               // no scene options: no branch queues
 
     __device__ __forceinline__ const DevScene& scene(int s) const { return slots[s].sc; }
-    // Warp-aggregated grab: the leader looks at the oldest kRingWindow
-    // published requests from first_active on and takes up to one sample per
-    // calling lane from the one with the fewest samples left, by an atomic
-    // add on its counter; -1 for every lane when none is left (or the
-    // attempts run out).  The result is slot << 40 | sample index.
+    // Warp-aggregated grab: the calling lanes look at the oldest kRingWindow
+    // published requests from first_active on (each lane at every n-th of
+    // them, n the number of calling lanes, then two warp reductions), and the
+    // leader takes up to one sample per calling lane from the one with the
+    // fewest samples left, by an atomic add on its counter; -1 for every lane
+    // when none is left (or the attempts run out).  The result is
+    // slot << 40 | sample index.  Remaining counts compare up to 2^26 - 1
+    // (larger ones as equal, the older first).
     __device__ __forceinline__ int64_t grab(unsigned long long*, unsigned lane) const
     {
         const unsigned m = __activemask();
         const int leader = __ffs(m) - 1;
         const unsigned rank = __popc(m & ((1u << lane) - 1u));
+        const unsigned cnt = __popc(m);
+        constexpr long long kRemCap = (1ll << 26) - 1;
         long long base = -1;
         unsigned n = 0;
-        if ((int)lane == leader) {
-            const unsigned long long want = (unsigned long long)__popc(m);
-            for (int it = 0; it < kRingGrabTries; ++it) {
-                const long long nreq = (long long)ld_acquire_u64(&ctl->nreq);
-                long long lo = (long long)ld_volatile_u64(&ctl->first_active);
+        for (int it = 0; it < kRingGrabTries; ++it) {
+            long long nreq = 0, lo = 0;
+            if ((int)lane == leader) {
+                nreq = (long long)ld_acquire_u64(&ctl->nreq);
+                lo = (long long)ld_volatile_u64(&ctl->first_active);
                 if (lo < nreq - kRingSlots) lo = nreq - kRingSlots;
                 if (lo < 0) lo = 0;
-                unsigned long long g[kRingWindow];
-                long long ns[kRingWindow];
-#pragma unroll
-                for (int q = 0; q < kRingWindow; ++q) {
-                    const long long k = lo + q;
-                    const int s = (int)(k % kRingSlots);
-                    g[q] = (k < nreq) ? ld_volatile_u64(&slots[s].grabbed) : 0ull;
-                    ns[q] = (k < nreq) ? slots[s].nsamples : 0ll;
+            }
+            nreq = __shfl_sync(m, nreq, leader);
+            lo = __shfl_sync(m, lo, leader);
+            const long long wend = (nreq - lo < kRingWindow) ? nreq - lo : kRingWindow;
+            unsigned key = 0xffffffffu, fq = kRingWindow;          // (remaining << 6 | q), first q with samples left
+            for (long long q = rank; q < wend; q += cnt) {
+                const int s = (int)((lo + q) % kRingSlots);
+                const long long rem = slots[s].nsamples - (long long)ld_volatile_u64(&slots[s].grabbed);
+                if (rem > 0) {                                       // <= 0 once the counter ran past
+                    if ((unsigned)q < fq) fq = (unsigned)q;
+                    const unsigned kk = ((unsigned)(rem < kRemCap ? rem : kRemCap) << 6) | (unsigned)q;
+                    if (kk < key) key = kk;
                 }
-                int best = -1, first = -1;
-                long long best_rem = 0;
-#pragma unroll
-                for (int q = 0; q < kRingWindow; ++q) {
-                    const long long rem = ns[q] - (long long)g[q];     // <= 0 once the counter ran past
-                    if (rem > 0) {
-                        if (first < 0) first = q;
-                        if (best < 0 || rem < best_rem) { best = q; best_rem = rem; }
+            }
+            key = __reduce_min_sync(m, key);
+            fq = __reduce_min_sync(m, fq);
+            int again = 0;
+            if ((int)lane == leader) {
+                // requests before the first one with samples left are done with
+                const long long adv = (fq < (unsigned)kRingWindow) ? lo + fq
+                                                                    : (lo + kRingWindow < nreq ? lo + kRingWindow : nreq);
+                if (adv > lo) atomicMax(&ctl->first_active, (unsigned long long)adv);
+                if (key == 0xffffffffu) {
+                    again = (lo + kRingWindow < nreq) ? 1 : 0;      // look further on, or none left
+                } else {
+                    // an atomic add always succeeds: the counter may run past the
+                    // request's samples, and what lies past them is not taken
+                    // (after a reuse of the slot: the new request's samples)
+                    const int s = (int)((lo + (long long)(key & 63u)) % kRingSlots);
+                    const unsigned long long want = cnt;
+                    const unsigned long long c = atomicAdd(&slots[s].grabbed, want);
+                    const long long have = slots[s].nsamples - (long long)c;
+                    if (have <= 0) {
+                        again = 1;
+                    } else {
+                        const unsigned long long t = (unsigned long long)have < want ? (unsigned long long)have : want;
+                        atomicAdd(&ctl->grabbed, t);
+                        base = ((long long)s << kRingLocalBits) | (long long)c;
+                        n = (unsigned)t;
                     }
                 }
-                // requests before the first one with samples left are done with
-                const long long adv = (first >= 0) ? lo + first : (lo + kRingWindow < nreq ? lo + kRingWindow : nreq);
-                if (adv > lo) atomicMax(&ctl->first_active, (unsigned long long)adv);
-                if (best < 0) {
-                    if (lo + kRingWindow < nreq) continue;        // look further on
-                    break;
-                }
-                // an atomic add always succeeds: the counter may run past the
-                // request's samples, and what lies past them is not taken
-                // (after a reuse of the slot: the new request's samples)
-                const int s = (int)((lo + best) % kRingSlots);
-                const unsigned long long c = atomicAdd(&slots[s].grabbed, want);
-                const long long have = slots[s].nsamples - (long long)c;
-                if (have <= 0) continue;
-                const unsigned long long t = (unsigned long long)have < want ? (unsigned long long)have : want;
-                atomicAdd(&ctl->grabbed, t);
-                base = ((long long)s << kRingLocalBits) | (long long)c;
-                n = (unsigned)t;
-                break;
             }
+            again = __shfl_sync(m, again, leader);
+            base = __shfl_sync(m, base, leader);
+            if (base >= 0 || !again) break;
         }
-        base = __shfl_sync(m, base, leader);
         n = __shfl_sync(m, n, leader);
         return (base >= 0 && rank < n) ? (int64_t)(base + rank) : -1;
     }
@@ -339,7 +349,16 @@ struct Request {
     Clock::time_point submitted, published, finished;
     int status;                        // RT_PENDING until done
     uint64_t rays;
+    int passed = 0;                    // later requests admitted before it (kMaxPassed)
 };
+
+// Admission takes queued requests in arrival order, but a request that fits
+// may pass queued ones that do not fit yet: a small request then need not
+// wait behind a large one for the budget a third holds.  No request is passed
+// more than kMaxPassed times; after that, admission waits for it.  The
+// worker looks kAdmitLookahead requests deep.
+constexpr int kMaxPassed = 32;
+constexpr size_t kAdmitLookahead = 64;
 
 struct Ring {
     int kind = -1;
@@ -609,20 +628,30 @@ static void worker_main(rt_server* S)
         for (Ring& g : S->rings)
             if (g.ready) ring_progress(S, g);
         if (S->stop && S->in_flight == 0 && !any_launch_running(S)) break;
-        // admit in arrival order while the budget, the ring and the arena allow
+        // admit in arrival order while the budget, the ring and the arena
+        // allow, letting a request that fits pass ones that do not (kMaxPassed)
         bool touched[kRingKinds] = {false, false, false, false, false, false};
-        while (!S->stop && !S->queue.empty()) {
-            Request& r = S->req[S->queue.front()];
-            if (S->in_use + r.bytes > S->budget) break;
+        size_t qi = 0;
+        while (!S->stop && qi < S->queue.size() && qi < kAdmitLookahead) {
+            Request& r = S->req[S->queue[qi]];
+            if (S->in_use + r.bytes > S->budget) {
+                if (r.passed >= kMaxPassed) break;
+                ++qi;
+                continue;
+            }
             Ring& g = S->rings[r.kind];
             if (!g.ready && ring_init(S, g, r.kind) != cudaSuccess) {
                 ring_free(g);
                 finish_request(S, r, RT_ECUDA, Clock::now());
-                S->queue.pop_front();
+                S->queue.erase(S->queue.begin() + (std::ptrdiff_t)qi);
                 S->cv_done.notify_all();
                 continue;
             }
-            if (g.slot_ticket[g.nreq % kRingSlots] != 0) break;          // the ring is full
+            if (g.slot_ticket[g.nreq % kRingSlots] != 0) {               // its ring is full
+                if (r.passed >= kMaxPassed) break;
+                ++qi;
+                continue;
+            }
             const rt_scene_desc& d = r.desc;
             const size_t npix = (size_t)d.height * (d.centre_line ? 1 : (size_t)d.width);
             size_t need = 0, need_cnt = 0;
@@ -640,18 +669,21 @@ static void worker_main(rt_server* S)
             if (!ok) {
                 if (S->in_flight == 0) {                                  // can never fit
                     finish_request(S, r, RT_ENOMEM, Clock::now());
-                    S->queue.pop_front();
+                    S->queue.erase(S->queue.begin() + (std::ptrdiff_t)qi);
                     S->cv_done.notify_all();
                     continue;
                 }
-                break;
+                if (r.passed >= kMaxPassed) break;
+                ++qi;
+                continue;
             }
             r.arena_off = off;
             r.arena_bytes = need;
             r.cnt_off = coff;
             r.cnt_bytes = need_cnt;
             S->in_use += r.bytes;
-            S->queue.pop_front();
+            for (size_t j = 0; j < qi; ++j) S->req[S->queue[j]].passed++;
+            S->queue.erase(S->queue.begin() + (std::ptrdiff_t)qi);
             S->in_flight++;
             if (publish(S, g, r) != cudaSuccess) {
                 g.slot_ticket[g.nreq % kRingSlots] = 0;

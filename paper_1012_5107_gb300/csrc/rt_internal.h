@@ -17,7 +17,10 @@ constexpr int kLaneVariants = 3;
 constexpr int kVariantBlocks[kLaneVariants] = {4, 5, 6};
 constexpr int kVariantWave = 3;
 constexpr int kDefaultVariant = kVariantWave;
-constexpr int kMinActive = 28;   // an integration task continues while at least this many of its 32 rays are inside the cloak
+// An integration task continues while at least this many of its 32 rays are
+// inside the cloak (the step's batched launch, the current RK4 kernel: 7.25 ms
+// at 24 and 26, 7.34 ms at 28, 7.87 ms at 30)
+constexpr int kMinActive = 24;
 // Dormand-Prince steps are longer: a task holding fewer rays is still worth
 // running (1920 x 1080 x 16 with one block of 384 threads per SM, E = 8 / 32:
 // 133.0 / 214.8 ms at 8, 135.1 / 221.5 ms at 16; 2 to 10 within 1 %)

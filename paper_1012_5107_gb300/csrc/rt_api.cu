@@ -317,7 +317,7 @@ int rt_create_scene(const rt_scene_desc* desc, rt_scene** out)
     build_dev(desc, &s->dev);
     int bps = 0;
     s->variant = kDefaultVariant;
-    s->min_active = default_min_active(desc->integrator);
+    s->min_active = default_min_active(desc->precision, render_mode(*desc));
     s->wait = WaitLimit{kDefaultWaitSpin, 0};
     cudaError_t e = desc->mirror == RT_MIRROR_GAUSS ? gauss_upload() : cudaSuccess;
     if (e == cudaSuccess) e = render_occupancy(desc->precision, render_mode(*desc), s->variant, desc->flags != 0, &bps);
@@ -476,7 +476,7 @@ int rt_scene_autotune(rt_scene* s, float* d_rgb, int32_t trials, void* stream, i
     char key[160];
     snprintf(key, sizeof key, "scene/p%d/i%d/c%d/m%d/f%d/log2n%d", d.precision, d.integrator, d.cloak, d.mirror, d.flags,
              (int)floor(log2(samples > 1.0 ? samples : 1.0)));
-    int v = kDefaultVariant, m = default_min_active(d.integrator);
+    int v = kDefaultVariant, m = default_min_active(d.precision, render_mode(d));
     if (!tune_lookup(key, &v, &m)) {
         const int cand[] = {12, 16, 20, 24, 28};
         cudaStream_t st = (cudaStream_t)stream;

@@ -245,7 +245,7 @@ int rt_batch_create(rt_scene* const* scenes, int32_t n, rt_batch** out)
     b->integrator = integrator;
     b->total = off[n];
     b->total_samples = soff[n];
-    b->min_active = default_min_active(integrator);
+    b->min_active = default_min_active(precision, integrator);
     b->graph_min_active = -1;
     b->h_rgbs.assign(n, nullptr);
     cudaError_t e = cudaMalloc(&b->d_scenes, sizeof(DevScene) * n);
@@ -449,7 +449,7 @@ int rt_batch_autotune(rt_batch* b, float* const* d_rgb, int32_t trials, void* st
     if (!tune_lookup(key, &v, &m)) {
         const int cand[] = {12, 16, 20, 24, 28};
         float best = 1e30f;
-        m = default_min_active(b->integrator);
+        m = default_min_active(b->precision, b->integrator);
         for (int c : cand) {
             b->min_active = c;
             float ms = 0.0f;

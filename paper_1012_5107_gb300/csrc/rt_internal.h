@@ -18,14 +18,25 @@ constexpr int kVariantBlocks[kLaneVariants] = {4, 5, 6};
 constexpr int kVariantWave = 3;
 constexpr int kDefaultVariant = kVariantWave;
 // An integration task continues while at least this many of its 32 rays are
-// inside the cloak (the step's batched launch, the current RK4 kernel: 7.25 ms
-// at 24 and 26, 7.34 ms at 28, 7.87 ms at 30)
-constexpr int kMinActive = 24;
+// inside the cloak.  Measured on the current kernels (CUDA events): the FP32
+// RK4 grating loop is fastest at 24 (the step's batched launch 7.25 ms, 7.34
+// at 28, 7.87 at 30); the FP64 loops, the time form and the Gaussian medium
+// at 28 (FP64 cloaked render 605 ms at 28, 624 at 24; FP32 time form 9.20 /
+// 9.35 ms; Gaussian 9.39 / 9.49 ms).
+constexpr int kMinActive = 28;
+constexpr int kMinActiveRK4F32 = 24;
 // Dormand-Prince steps are longer: a task holding fewer rays is still worth
 // running (1920 x 1080 x 16 with one block of 384 threads per SM, E = 8 / 32:
 // 133.0 / 214.8 ms at 8, 135.1 / 221.5 ms at 16; 2 to 10 within 1 %)
 constexpr int kMinActiveDP45 = 8;
-inline int default_min_active(int integrator) { return integrator == RT_DP45 ? kMinActiveDP45 : kMinActive; }
+// The default for a precision (RT_FP32 / RT_FP64) and render mode (the
+// integrator, with kModeGauss for the Gaussian bump).
+inline int default_min_active(int precision, int mode)
+{
+    if ((mode & 7) == RT_DP45) return kMinActiveDP45;
+    if (precision == RT_FP32 && mode == RT_RK4) return kMinActiveRK4F32;
+    return kMinActive;
+}
 constexpr int kMaxWindows = 16;
 // Render mode: the integrator (RT_RK4, RT_DP45, RT_RK4T), with kModeGauss set
 // for scenes of the Gaussian bump, whose box holds the Gaussian map's medium.

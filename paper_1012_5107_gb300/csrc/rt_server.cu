@@ -232,7 +232,7 @@ static cudaError_t ring_launch_t(int grid, RingSlot* slots, RingCtl* ctl, RingDo
         set.fetch_or(bit);
     }
     wave_ring_kernel<R, INTEG><<<grid, WaveShape<R, INTEG>::kBlock, wave_smem_bytes<R, INTEG>(), st>>>(slots, ctl, done, counters,
-                                                                               default_min_active(INTEG));
+                                                                               default_min_active(sizeof(R) == 4 ? RT_FP32 : RT_FP64, INTEG));
     return cudaGetLastError();
 }
 

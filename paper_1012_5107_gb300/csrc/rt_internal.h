@@ -20,11 +20,13 @@ constexpr int kDefaultVariant = kVariantWave;
 // An integration task continues while at least this many of its 32 rays are
 // inside the cloak.  Measured on the current kernels (CUDA events): the FP32
 // RK4 grating loop is fastest at 24 (the step's batched launch 7.25 ms, 7.34
-// at 28, 7.87 at 30); the FP64 loops, the time form and the Gaussian medium
-// at 28 (FP64 cloaked render 605 ms at 28, 624 at 24; FP32 time form 9.20 /
-// 9.35 ms; Gaussian 9.39 / 9.49 ms).
+// at 28, 7.87 at 30); the FP32 time form and Gaussian medium at 28 (time form
+// 9.21 ms, 9.35 at 24, 9.47 at 30; Gaussian 9.39 / 9.49 ms at 28 / 24); the
+// FP64 loops, bound by the FP64 pipe, with full warps only (FP64 cloaked
+// render 590 ms at 32, 595 at 30, 605 at 28, 623 at 24).
 constexpr int kMinActive = 28;
 constexpr int kMinActiveRK4F32 = 24;
+constexpr int kMinActiveF64 = 32;
 // Dormand-Prince steps are longer: a task holding fewer rays is still worth
 // running (1920 x 1080 x 16 with one block of 384 threads per SM, E = 8 / 32:
 // 133.0 / 214.8 ms at 8, 135.1 / 221.5 ms at 16; 2 to 10 within 1 %)
@@ -34,7 +36,8 @@ constexpr int kMinActiveDP45 = 8;
 inline int default_min_active(int precision, int mode)
 {
     if ((mode & 7) == RT_DP45) return kMinActiveDP45;
-    if (precision == RT_FP32 && mode == RT_RK4) return kMinActiveRK4F32;
+    if (precision == RT_FP64) return kMinActiveF64;
+    if (mode == RT_RK4) return kMinActiveRK4F32;
     return kMinActive;
 }
 constexpr int kMaxWindows = 16;

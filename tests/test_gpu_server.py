@@ -181,3 +181,37 @@ def test_ring_wraps_around(rt):
     st = server.stats()
     assert st["completed"] == n and st["in_flight"] == 0 and st["bytes_in_use"] == 0
     server.close()
+
+
+def test_small_request_passes_one_waiting_for_budget(rt):
+    """Admission under a budget that holds one large request and one small
+    one: a second large request must wait for the first, but a small request
+    submitted after it is admitted at once (it passes the waiting one) and
+    finishes before it; every result equals the render alone."""
+    import torch
+    big1 = inputs.base_scene(width=1024, height=1024, spp=16, seed=31, scene_id=1, precision=0)
+    big2 = inputs.base_scene(width=1024, height=1024, spp=16, seed=32, scene_id=2, precision=0)
+    small = inputs.base_scene(width=48, height=40, spp=4, seed=33, scene_id=3, precision=0)
+    budget = rt.request_bytes(big1) + rt.request_bytes(small)
+    assert rt.request_bytes(big1) + rt.request_bytes(big2) > budget
+    ref = torch.zeros((40, 48, 3), dtype=torch.float32, device="cuda")
+    sc = rt.Scene(small)
+    sc.render(ref)
+    torch.cuda.synchronize()
+    server = rt.Server(budget_bytes=budget, max_inflight=2)
+    outs = [torch.zeros((1024, 1024, 3), dtype=torch.float32, device="cuda") for _ in range(2)]
+    out_small = torch.full((40, 48, 3), -1.0, dtype=torch.float32, device="cuda")
+    t1 = server.submit(big1, outs[0])
+    t2 = server.submit(big2, outs[1])
+    ts = server.submit(small, out_small)
+    res = wait_all(server, [t1, t2, ts])
+    assert len(res) == 3 and all(r["status"] == 0 for r in res.values())
+    r1, r2, rs = res[t1], res[t2], res[ts]
+    # the second large request waited for the first one's budget; the small
+    # one did not wait for either
+    assert r2["queue_ms"] > 0.5 * r1["latency_ms"]
+    assert rs["queue_ms"] < 0.25 * r1["latency_ms"]
+    assert rs["latency_ms"] < r1["latency_ms"] < r2["latency_ms"]
+    torch.cuda.synchronize()
+    assert torch.equal(out_small, ref)
+    server.close()

@@ -1548,6 +1548,33 @@ __device__ void air_segment(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phas
 // ------------------------------------------------------------------------
 // Service of a lane whose step crossed a surface (or hit a guard).
 // ------------------------------------------------------------------------
+// The FP32 RK4 step in the grating cloak is committed in place, also when it
+// crossed a surface: the event service then rebuilds the step's start as one
+// step of -h from its end (rebuild_start).  Keeping the start live through
+// every step, for the one step in hundreds that crosses, costs a conditional
+// copy of the whole state per step.  The rebuilt start differs from the true
+// one by the integrator's local error, O(h^5): at h = Lambda/200 in the
+// benchmark cloak (kA = 3/8), a forward and a backward step of the FP64
+// oracle return within 7e-10 Lambda in position and 4e-8 in momentum, about
+// one FP32 rounding of the momentum.  FP64 keeps the start (its rays match
+// the oracle's to 1e-12).
+template <class R, int INTEG>
+__host__ __device__ constexpr bool back_start()
+{
+    return sizeof(R) == 4 && integ_of(INTEG) == RT_RK4 && !gauss_of(INTEG);
+}
+
+// The start of the step that ended at b (back_start): one step of -h, the
+// force formed as at the end of a step.
+template <class R, int INTEG>
+__device__ __forceinline__ void rebuild_start(const StepConst<R>& k, Box<R>& b, R h, LaneStats& st)
+{
+    Box<R> s0;
+    integ_step<R, INTEG>(k, b, -h, s0, st);
+    ray_force(s0.wr, s0.wi, s0.rr, s0.ri, k.fk, s0.Fx, s0.Fy);
+    b = s0;
+}
+
 template <class R, int INTEG, bool OPT>
 __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& phase, int& surf, int steps,
                               rt_ray_record* rec, LaneStats& st)
@@ -1566,6 +1593,7 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
         finish_sample<R, OPT>(sc, C, steps, RT_RAY_NAN, phase, rec);
         return;
     }
+    if constexpr (back_start<R, INTEG>()) rebuild_start<R, INTEG>(k, b, C.hs, st);   // b held the step's end
     int ev_best = EV_NONE, last = EV_NONE;
     R th_best = R(2);
     Box<R> t;
@@ -1799,9 +1827,19 @@ template <class R, int INTEG>
 __device__ __forceinline__ void box_step(const StepConst<R>& k, int64_t max_steps, Cold<R>& C, Box<R>& b, int& phase,
                                          int& surf, int& steps, LaneStats& st, int& safe)
 {
-    Box<R> o;
-    box_step_into<R, INTEG>(k, max_steps, C, b, o, phase, surf, steps, st, safe);
-    if (phase == PH_BOX) b = o;
+    if constexpr (back_start<R, INTEG>()) {
+        if (steps >= max_steps) {
+            phase = PH_GUARD;
+            return;
+        }
+        Box<R> o;
+        box_step_into<R, INTEG>(k, max_steps, C, b, o, phase, surf, steps, st, safe);
+        b = o;
+    } else {
+        Box<R> o;
+        box_step_into<R, INTEG>(k, max_steps, C, b, o, phase, surf, steps, st, safe);
+        if (phase == PH_BOX) b = o;
+    }
 }
 
 // ------------------------------------------------------------------------

@@ -40,9 +40,12 @@
  *     n/n_min in [1, 2.2]; its box spans y = 0 (the flat mirror) to H;
  *   - the photograph (Fig. 2a) is replaced by a synthetic background plane.
  *
- * Parity unpinned: 3-D rays (p_z != 0) and total internal reflection at the
- * side faces are pinned only through invariants (|p| = n, p_z conserved),
- * step-size convergence and RK4/DP45 agreement; there is no closed form.
+ * 3-D rays (p_z != 0) are pinned by their planar part: (x, y, p_x, p_y)
+ * evolve exactly as those of the same ray with p_z = 0 while z moves
+ * linearly; total internal reflection at the side faces by the reflection
+ * law, component by component, at the +x and +z faces
+ * (tests/test_oracle_box_faces.py); refraction at the faces by the plate's
+ * parallel displacement (tests/test_oracle_fresnel.py).
  */
 #include <complex.h>
 #include <float.h>

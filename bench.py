@@ -55,7 +55,7 @@ MUFU_PER_NEWTON = 4
 # renders): dram__bytes_read.sum + dram__bytes_write.sum of an ncu capture
 # (--set full, one launch) of the current kernel; None until that capture
 # exists or after the kernel changes.
-TRAFFIC_BATCH_BYTES = 7_867_392 + 2_913_024
+TRAFFIC_BATCH_BYTES = None
 
 
 def peaks():

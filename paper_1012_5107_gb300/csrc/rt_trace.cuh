@@ -1722,10 +1722,10 @@ __device__ void service_event(const DevScene& sc, Cold<R>& C, Box<R>& b, int& ph
 // ------------------------------------------------------------------------
 // One step from s into o.  Accepted (phase stays PH_BOX): the new state is in
 // o.  A rejected Dormand-Prince attempt also leaves phase at PH_BOX, with o a
-// copy of s and a smaller next step.  A step that crosses a surface, goes
-// non-finite (PH_EVENT) or hits the step cap (PH_GUARD) leaves the state in s
-// and o undefined.  Writing into a second state lets the caller alternate
-// between two states instead of copying the new one back every step.
+// copy of s and a smaller next step.  A step that crosses a surface or goes
+// non-finite (PH_EVENT) leaves the step's end in o: box_step keeps s for the
+// event service, except on the back_start paths, which keep o and rebuild s
+// from it.  A step cap reached (PH_GUARD) leaves o undefined.
 // RK4 in the grating cloak skips the box faces' tests while the ray is
 // farther from every face than `safe` steps can move it (isafe: one over the
 // largest move of a step); the grating's test runs every step.

@@ -372,13 +372,15 @@ def run_gpu(args):
     host, hc, hl = hosts[(n_e2e - 1) % 2]
     d2h = sum(h.numel() * 4 for h in host.values()) + hc.numel() * 8 + hl.numel() * 8
 
-    xmap = bench_xcorr_map(rt, torch, step, stream, clock_mhz)
-    table1 = None if args.no_table1 else bench_table1(rt, torch, stream)
-    hd = None if args.no_hd else bench_hd(rt, torch, stream)
-    tform = None if args.no_time_form else bench_time_form(rt, torch, stream)
-    gauss = None if args.no_gauss else bench_gauss_fig4(rt, torch, stream)
-    batch = None if args.no_batch else bench_batch(rt, torch, stream)
-    serving = None if args.no_serving else bench_serving(rt, torch)
+    # the secondary legs: a failure is reported in the leg's field (its
+    # traceback on stderr) instead of losing the line measured above
+    xmap = guarded(bench_xcorr_map, rt, torch, step, stream, clock_mhz)
+    table1 = None if args.no_table1 else guarded(bench_table1, rt, torch, stream)
+    hd = None if args.no_hd else guarded(bench_hd, rt, torch, stream)
+    tform = None if args.no_time_form else guarded(bench_time_form, rt, torch, stream)
+    gauss = None if args.no_gauss else guarded(bench_gauss_fig4, rt, torch, stream)
+    batch = None if args.no_batch else guarded(bench_batch, rt, torch, stream)
+    serving = None if args.no_serving else guarded(bench_serving, rt, torch)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -390,7 +392,7 @@ def run_gpu(args):
             sc.render_pixels(pix, rgb, rec, stream=stream)
             torch.cuda.synchronize()
             return rt.records_to_numpy(rec)
-        cpu = cpu_baseline(args.cpu_seconds, gpu_records)
+        cpu = guarded(cpu_baseline, args.cpu_seconds, gpu_records)
 
     lat = {"p50_ms": round(float(np.percentile(step_ms, 50)), 3), "p99_ms": round(float(np.percentile(step_ms, 99)), 3)}
     line = {
@@ -768,6 +770,17 @@ def bench_serving(rt, torch) -> dict:
     out["load_80_percent"] = serve_leg(rt, torch, rate=0.8 * capacity, count=200,
                                        rays_per_s=sat["Mrays_per_s"] * 1e6)
     return out
+
+
+def guarded(fn, *args, **kwargs):
+    """One secondary leg of the bench: its result, or {"error": ...} with the
+    traceback on stderr if it raised."""
+    try:
+        return fn(*args, **kwargs)
+    except Exception as e:                             # noqa: BLE001 -- reported, not hidden
+        import traceback
+        traceback.print_exc(file=sys.stderr)
+        return {"error": f"{type(e).__name__}: {e}"[:400]}
 
 
 def cpu_baseline(seconds: float, gpu_records=None) -> dict:
